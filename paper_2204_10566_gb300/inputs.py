@@ -1,0 +1,160 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmark and the oracle.
+
+This module holds no lattice Boltzmann arithmetic: only geometry (flag
+fields), workload descriptions, and seeded random numbers.  Both sides of a
+parity test take their inputs from here and compute everything else on their
+own.
+
+Geometry: the FDA benchmark nozzle of Sec. 2.2 (axisymmetric: inlet pipe,
+conical contraction, throat, sudden expansion) voxelised on a box whose axis
+is z.  The real FDA CAD lengths are in a figure the text does not carry, so the
+lengths follow the workload definitions below: inlet pipe diameter D = 3 d
+(the inlet/throat Reynolds ratio of 3 quoted in Sec. 3), inlet pipe length D,
+a 10-degree half-angle cone, a 4 d throat, and the expansion pipe for the rest.
+Voxel (x, y, z) is inside iff (x+1/2-D/2)^2 + (y+1/2-D/2)^2 <= r(z+1/2)^2.
+
+Flag values: 0 SOLID, 1 FLUID, 2 INLET (plane z = 0), 3 OUTLET (plane z = nz-1).
+"""
+import math
+
+import numpy as np
+
+SOLID, FLUID, INLET, OUTLET = 0, 1, 2, 3
+
+
+def cone_length(D, d, half_angle_deg=10.0):
+    """Axial length of a cone from radius D/2 to d/2 at the given half-angle."""
+    return int(round((D - d) / 2.0 / math.tan(math.radians(half_angle_deg))))
+
+
+def nozzle_radius(z_centre, D, d, L_in, L_cone, L_throat, half_angle_deg=10.0):
+    """Wall radius r(z) of the nozzle at axial position z_centre (cells).  In
+    the cone the wall keeps the true half-angle, r = D/2 - (z - L_in) tan(angle),
+    never below d/2 (L_cone is rounded to whole cells)."""
+    if z_centre < L_in:
+        return D / 2.0
+    if z_centre < L_in + L_cone:
+        r = D / 2.0 - (z_centre - L_in) * math.tan(math.radians(half_angle_deg))
+        return max(r, d / 2.0)
+    if z_centre < L_in + L_cone + L_throat:
+        return d / 2.0
+    return D / 2.0
+
+
+def nozzle_flags(D, d, L_total, L_in=None, L_cone=None, L_throat=None, half_angle_deg=10.0,
+                 inlet=True, outlet=True):
+    """Flag field (nz, ny, nx) = (L_total, D, D) of the voxelised nozzle."""
+    L_in = D if L_in is None else L_in
+    L_cone = cone_length(D, d, half_angle_deg) if L_cone is None else L_cone
+    L_throat = 4 * d if L_throat is None else L_throat
+    c = np.arange(D) + 0.5 - D / 2.0
+    r2 = c[None, :] ** 2 + c[:, None] ** 2          # [y, x]
+    flags = np.zeros((L_total, D, D), dtype=np.uint8)
+    for z in range(L_total):
+        r = nozzle_radius(z + 0.5, D, d, L_in, L_cone, L_throat, half_angle_deg)
+        flags[z][r2 <= r * r] = FLUID
+    if inlet:
+        flags[0][flags[0] == FLUID] = INLET
+    if outlet:
+        flags[-1][flags[-1] == FLUID] = OUTLET
+    return flags
+
+
+def pipe_flags(D, L_total, inlet=True, outlet=True):
+    """Straight circular pipe of diameter D (cells) along z."""
+    return nozzle_flags(D, D, L_total, L_in=L_total, L_cone=1, L_throat=0, inlet=inlet, outlet=outlet)
+
+
+def box_flags(nx, ny, nz):
+    """All-fluid box (use with periodic boundaries)."""
+    return np.full((nz, ny, nx), FLUID, dtype=np.uint8)
+
+
+def channel_flags(nx, ny, nz):
+    """All-fluid box whose y faces are walls when y is not periodic."""
+    return box_flags(nx, ny, nz)
+
+
+def active_count(flags):
+    return int(np.count_nonzero(flags != SOLID))
+
+
+# ------------------------------------------------------------------ workloads
+
+WORKLOADS = {
+    # Re 500 laminar nozzle: D = 24, d = 8, lengths 24/45/32/59, plug inlet.
+    "nozzle_re500_24x24x160": dict(kind="nozzle", D=24, d=8, L_total=160, Re=500.0, u_throat=0.05,
+                                   profile="plug", noise=0.0, seed=0, steps=200),
+    # Re 3500 transitional nozzle: D = 96, d = 32, parabolic inlet + 1 % noise.
+    "nozzle_re3500_96x96x800": dict(kind="nozzle", D=96, d=32, L_total=800, Re=3500.0, u_throat=0.05,
+                                    profile="parabolic", noise=0.01, seed=1, steps=20000),
+    # Re 6500 under-resolved turbulent nozzle: D = 144, d = 48, parabolic + 2 % noise.
+    "nozzle_re6500_144x144x1200": dict(kind="nozzle", D=144, d=48, L_total=1200, Re=6500.0,
+                                       u_throat=0.05, profile="parabolic", noise=0.02, seed=2,
+                                       steps=50000),
+    # Periodic Taylor-Green vortex, 256^3, u0 = 0.04.
+    "tgv_256": dict(kind="tgv", n=256, u0=0.04, Re=1600.0, steps=1000),
+}
+
+
+def workload_flags(name):
+    w = WORKLOADS[name]
+    if w["kind"] == "nozzle":
+        return nozzle_flags(w["D"], w["d"], w["L_total"])
+    if w["kind"] == "pipe":
+        return pipe_flags(w["D"], w["L_total"])
+    if w["kind"] == "tgv":
+        return box_flags(w["n"], w["n"], w["n"])
+    raise KeyError(name)
+
+
+def inlet_mean_velocity(w):
+    """Mean inlet velocity u0 = u_throat (d/D)^2 (Sec. 2.2 throat-velocity relation)."""
+    return w["u_throat"] * (w["d"] / w["D"]) ** 2
+
+
+# ------------------------------------------------------------- random fields
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+def random_uniform(shape, amplitude, seed):
+    """Uniform numbers in [-amplitude, amplitude) with a fixed seed."""
+    return amplitude * (2.0 * rng(seed).random(shape) - 1.0)
+
+
+def random_velocity_field(n, amplitude, seed):
+    """(n, 3) velocities, uniform in [-amplitude, amplitude)."""
+    return random_uniform((n, 3), amplitude, seed)
+
+
+def random_density_field(n, amplitude, seed):
+    """(n,) densities 1 + uniform in [-amplitude, amplitude)."""
+    return 1.0 + random_uniform((n,), amplitude, seed)
+
+
+def serving_requests(n=64, seed=2204, rate=None, d_range=(8, 48), re_range=(500.0, 6500.0),
+                     steps_range=(2000, 20000), scale=1.0):
+    """Seeded request stream for the serving loop: Poisson arrivals, nozzle or
+    pipe geometries of throat diameter d (D = 3 d, L = 25 d, each scaled by
+    ``scale``), Re uniform in re_range, step counts uniform in steps_range,
+    storage FP32 or FP16-shifted with probability 1/2."""
+    g = rng(seed)
+    rate = 1.0 if rate is None else rate
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += g.exponential(1.0 / rate)
+        d = int(g.integers(d_range[0], d_range[1] + 1))
+        d = max(4, int(round(d * scale)))
+        out.append(dict(
+            id=k,
+            arrival=t,
+            kind="nozzle" if g.random() < 0.5 else "pipe",
+            d=d, D=3 * d, L_total=25 * d,
+            Re=float(g.uniform(*re_range)),
+            steps=int(g.integers(steps_range[0], steps_range[1] + 1)),
+            precision="fp32" if g.random() < 0.5 else "fp16s",
+        ))
+    return out
