@@ -1,0 +1,390 @@
+"""Benchmark of the fused D3Q27 central-Hermite MRT stream-collide step on GB300.
+
+One "step" is one lattice time step over the whole workload (one fused
+kernel launch: pull gather, collision, bounce-back, inlet/outlet).  Default
+workload: the Re 3500 transitional nozzle on a 96 x 96 x 800 lattice
+(4 286 996 active cells), FP32 populations; FP16-shifted and FP64 storage are
+timed on the same workload for the precision comparison.  Inputs are seeded
+and synthetic; the population buffers (>= 0.28 GB each) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (a bounded sample of the same workload per step).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fluid MLUPS & % HBM roofline (FP32/FP16 vs FP64); serving p50/p99 latency"
+UNIT = "fluid MLUPS"
+DEFAULT_WORKLOAD = "nozzle_re3500_96x96x800"
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16 storage / f32 arithmetic"}
+LINK_WORD_BYTES = 4
+
+
+def algorithmic_bytes_per_cell(precision):
+    """27 populations read + 27 written in the storage precision, plus the
+    32-bit link word of the cell."""
+    return 27 * 2 * STORAGE_BYTES[precision] + LINK_WORD_BYTES
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precisions", default="fp32,fp16s,fp64",
+                    help="first one is the headline; others are reported under by_precision")
+    ap.add_argument("--fp64-steps", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_device.cuh", "lbm_internal.h", "step_fp32.cu", "step_fp16s.cu", "step_fp64.cu"):
+        with open(os.path.join(ROOT, "paper_2204_10566_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, precision):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, or None when missing or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        kv = dict(item.split("=", 1) for item in line.split())
+        if kv.get("workload") == workload and kv.get("precision") == precision and kv.get("source") == src:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_setup(name):
+    from paper_2204_10566_gb300 import inputs as I
+
+    w = I.WORKLOADS[name]
+    flags = I.workload_flags(name)
+    if w["kind"] == "tgv":
+        params = dict(nu=w["u0"] * (w["n"] / (2 * 3.141592653589793)) / w["Re"])
+        periodic = 7
+    else:
+        params = dict(Re=w["Re"], u_char=w["u_throat"], L_char=float(w["d"]), u_in=I.inlet_mean_velocity(w),
+                      d_in=float(w["D"]), profile=w["profile"], noise_amp=w["noise"], noise_seed=w["seed"])
+        periodic = 0
+    return w, flags, params, periodic
+
+
+# --------------------------------------------------------------- our kernels
+
+def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup, dist=None, sampler=None):
+    from paper_2204_10566_gb300 import inputs as I
+
+    G = lbm.Lattice(flags, precision, periodic=periodic)
+    G.set_params(**params)
+    n = G.n_active
+    G.init_fields(I.random_density_field(n, 0.001, 3), I.random_velocity_field(n, 0.01, 4))
+    G.step(warmup).sync()
+    stream = G.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0.record(stream)
+    G.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        dist.barrier()
+    G.sync()
+    ms = e0.elapsed_time(e1)
+    info = G.layout_info()
+    G.close()
+    return n, ms, clocks, info
+
+
+def e2e_run(lbm, torch, flags, params, periodic, precision, steps):
+    """The user's job through the public API with host buffers: upload the
+    initial fields from pinned host memory, run the steps, read the moments
+    back into pinned host memory; wall-clock timed."""
+    from paper_2204_10566_gb300 import inputs as I
+
+    G = lbm.Lattice(flags, precision, periodic=periodic)
+    G.set_params(**params)
+    n = G.n_active
+    rho_h = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    u_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    rho_o = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    u_o = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    rho_h[:] = I.random_density_field(n, 0.001, 3)
+    u_h[:] = I.random_velocity_field(n, 0.01, 4)
+    G.init_fields(rho_h, u_h)
+    G.step(10).sync()                      # warm the path once
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.init_fields(rho_h, u_h)
+    G.step(steps)
+    G.moments(out=(rho_o, u_o))
+    t1 = time.perf_counter()
+    G.close()
+    return dict(value=n * steps / (t1 - t0) / 1e6, unit=UNIT,
+                h2d_bytes_per_step=n * 4 * 8 / steps, d2h_bytes_per_step=n * 4 * 8 / steps,
+                seconds=t1 - t0, steps=steps)
+
+
+# ------------------------------------------------------------ oracle sample
+
+class OracleSample:
+    """The FP64 CPU oracle on a sub-box of the workload (a z-slab from the
+    middle of the lattice, cut in y when one plane is already too much),
+    sized from a one-plane calibration to about target_seconds per step."""
+
+    def __init__(self, flags, params, periodic, target_seconds):
+        import numpy as np
+
+        import oracle
+
+        self.oracle = oracle
+        nz, ny, nx = flags.shape
+        nu = params.get("nu") or params["u_char"] * params["L_char"] / params["Re"]
+        self.omega = 1.0 / (3.0 * nu + 0.5)
+        self.periodic = periodic & 3
+        z0 = nz // 2
+        plane = np.array(flags[z0:z0 + 1])
+        dt, cells = self._run(plane)
+        per_cell = dt / max(cells, 1)
+        want = max(1, int(target_seconds / per_cell))
+        if want >= cells:
+            planes, rows = min(nz - z0, max(1, want // max(cells, 1))), ny
+        else:
+            planes, rows = 1, max(2, int(ny * want / max(cells, 1)))
+        self.flags = np.array(flags[z0:z0 + planes, :rows, :])
+        self.cells = int((self.flags != 0).sum())
+        self.threads = os.cpu_count() or 1
+        self.desc = "1 oracle step on a %dx%dx%d sub-box (z from %d) of the workload, %d active cells" % (
+            nx, rows, planes, z0, self.cells)
+
+    def _run(self, f):
+        L = self.oracle.Lattice(f, self.omega, periodic=self.periodic)
+        L.init_equilibrium(1.0, [0.0, 0.0, 0.01])
+        t = time.perf_counter()
+        L.step(1)
+        return time.perf_counter() - t, int((f != 0).sum())
+
+    def step(self):
+        """One timed sample; returns (MLUPS, seconds)."""
+        dt, cells = self._run(self.flags)
+        return cells / dt / 1e6, dt
+
+
+# ------------------------------------------------------------------ arms
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    w, flags, params, periodic = workload_setup(args.workload)
+    total = args.steps + args.warmup
+    # each step a bounded sample, so that the whole run fits in ~150 s
+    sample = OracleSample(flags, params, periodic, max(0.002, 150.0 / max(total, 1)))
+    vals = []
+    t_all = 0.0
+    for k in range(total):
+        mlups, dt = sample.step()
+        if k >= args.warmup:
+            vals.append(mlups)
+            t_all += dt
+    threads, desc = sample.threads, sample.desc
+    value = statistics.median(vals) if vals else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(len(vals), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ours_arm(args):
+    import torch
+
+    from paper_2204_10566_gb300 import build as lbuild
+
+    lbuild.build()
+    from paper_2204_10566_gb300 import lbm
+
+    rank, world, local = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = td
+    else:
+        torch.cuda.set_device(0)
+    device = torch.cuda.current_device()
+    w, flags, params, periodic = workload_setup(args.workload)
+    precisions = args.precisions.split(",")
+    head = precisions[0]
+    peak, peak_kind = load_peaks()
+
+    sampler = ClockSampler(device) if rank == 0 else None
+    n, ms, clocks, info = time_precision(lbm, torch, flags, params, periodic, head, args.steps, args.warmup, dist,
+                                         sampler)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * n * args.steps / (ms_max * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / max(args.steps, 1)
+    alg_bytes = algorithmic_bytes_per_cell(head) * n
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = recorded_traffic(args.workload, head)
+
+    by_prec = {}
+    for p in precisions[1:]:
+        steps = args.fp64_steps if p == "fp64" else args.steps
+        n_p, ms_p, _, info_p = time_precision(lbm, torch, flags, params, periodic, p, steps,
+                                              min(args.warmup, 20), dist, None)
+        ach_p = algorithmic_bytes_per_cell(p) * n_p / (ms_p * 1e-3 / steps) / 1e9
+        by_prec[p] = {"value": world * n_p * steps / (ms_p * 1e-3) / 1e6, "unit": UNIT, "steps": steps,
+                      "ms_per_step": ms_p / steps,
+                      "roofline": {"bound": "hbm", "achieved": ach_p, "peak": peak, "unit": "GB/s",
+                                   "frac": ach_p / peak, "peak_kind": peak_kind,
+                                   "bytes_per_cell": algorithmic_bytes_per_cell(p)}}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    e2e = e2e_run(lbm, torch, flags, params, periodic, head, args.steps)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        sample = OracleSample(flags, params, periodic, args.cpu_seconds)
+        mlups, dt = sample.step()
+        cpu = {"value": mlups, "unit": UNIT, "cores": sample.threads, "kind": "oracle", "sample": sample.desc,
+               "seconds": dt}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
+        "config": {"workload": args.workload, "precision": head, "active_cells": n, "box": list(flags.shape[::-1]),
+                   "slots": info["slots"], "Re": w.get("Re"),
+                   "l2": "inputs larger than L2 (population buffers %.2f GB each)" % (info["buffer_bytes"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_step<%s>" % head,
+                     "bytes_per_cell": algorithmic_bytes_per_cell(head)},
+        "by_precision": by_prec,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours_arm(args)
+
+
+if __name__ == "__main__":
+    main()

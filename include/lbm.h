@@ -1,0 +1,237 @@
+/*
+ * lbm.h -- C ABI of a GB300 (sm_103a) D3Q27 lattice Boltzmann solver with the
+ * central-Hermite-moment multiple-relaxation-time collision of
+ * "Simulation of the FDA Nozzle Benchmark: A Lattice Boltzmann Study"
+ * (arXiv 2204.10566).
+ *
+ * One call of lbm_step advances every active cell of the lattice by one time
+ * step with a single fused pull-stream/collide kernel:
+ *   f_i(x + c_i, t + 1) - f_i(x, t) = T^-1 S T (f^eq(rho, u) - f)(x, t)
+ * (Sec. 2.1, MRT evolution eq.), T the central Hermite transform
+ * (Sec. 2.1, central moment eq.; Appendix A), f^eq the full Hermite expansion
+ * supported by D3Q27 (Sec. 2.1 equilibrium eq.; Appendix A), second-order
+ * moments relaxed at omega = 1/(3 nu + 1/2) (Sec. 2.1 relaxation-time relation)
+ * and higher orders at the ghost rates (1 by default, Appendix A), with
+ * halfway bounce-back walls, a velocity inlet and a constant-pressure outlet
+ * by non-equilibrium extrapolation (Sec. 2.2, "Simulation details").
+ *
+ * Conventions shared by every call
+ *   - Lattice units: dr = dt = 1, theta0 = 1/3.
+ *   - Direction i = 9 (cz+1) + 3 (cy+1) + (cx+1), c in {-1,0,1}^3; the
+ *     opposite direction is 26 - i.
+ *   - Box cell b = x + nx (y + ny z) ("x fastest").
+ *   - Active cells are the cells whose flag is FLUID, INLET or OUTLET.  The
+ *     "active order" lists them by increasing b.  Host arrays use either that
+ *     order (LBM_LAYOUT_ACTIVE, n = number of active cells) or the full box
+ *     (LBM_LAYOUT_BOX, n = nx ny nz, solid cells written as 0 and ignored on input).
+ *   - Population arrays are [n][27] doubles holding f_i (not deviations).
+ *   - Velocity arrays are [n][3] doubles.
+ *   - Every pointer argument is a HOST pointer unless the comment says
+ *     otherwise; the library copies what it needs and the caller keeps ownership.
+ *   - Every call returns an lbm_status.  No call throws or aborts.  After an
+ *     error, lbm_last_error(ctx) describes it; the string is owned by ctx and
+ *     valid until the next call on ctx.
+ *   - Device work is enqueued on the context's stream.  Calls that return
+ *     host data synchronise that stream; lbm_step does not.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument, inconsistent geometry or parameters */
+    LBM_ERR_OOM = 2,      /* device allocation failed / does not fit */
+    LBM_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    LBM_ERR_STATE = 4,    /* call out of order (e.g. lbm_step before lbm_set_geometry) */
+    LBM_ERR_UNSTABLE = 5, /* a health check found non-finite populations */
+    LBM_ERR_TIMEOUT = 6   /* a bounded device-side wait gave up */
+} lbm_status;
+
+typedef enum {
+    LBM_FP64 = 0,  /* populations stored as FP64 deviations f_i - w_i, FP64 arithmetic */
+    LBM_FP32 = 1,  /* FP32 deviations f_i - w_i, FP32 arithmetic */
+    LBM_FP16S = 2  /* FP16 (f_i - w_i) * s, FP32 arithmetic */
+} lbm_precision;
+
+enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
+enum { LBM_PROFILE_PLUG = 0, LBM_PROFILE_PARABOLIC = 1 };
+enum { LBM_LAYOUT_ACTIVE = 0, LBM_LAYOUT_BOX = 1 };
+enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Device memory provider.  alloc(bytes, user) returns a device pointer
+ * (256-byte aligned) or NULL; free(ptr, user) releases it.  With alloc == NULL
+ * the library uses cudaMalloc / cudaFree.  Called only from lbm_create,
+ * lbm_set_geometry, lbm_stats_begin, the population/field transfer calls and
+ * lbm_destroy, never from lbm_step. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} lbm_allocator;
+
+/* Lattice and device description (lbm_create). */
+typedef struct {
+    int32_t nx, ny, nz;   /* box size in cells, each >= 1 */
+    int32_t periodic;     /* LBM_PERIODIC_* bits; other faces are solid walls */
+    int32_t precision;    /* lbm_precision */
+    float fp16_scale;     /* FP16S scale s: a power of two > 0 (0 selects 4096 = 2^12, which keeps
+                             deviations of 1e-4..10 in the normal FP16 range) */
+    int32_t device;       /* CUDA device ordinal */
+    void *stream;         /* cudaStream_t for all work of this context (NULL: default stream) */
+    lbm_allocator allocator;
+} lbm_desc;
+
+/* Flow parameters (lbm_set_params).  Fill with lbm_params_default first. */
+typedef struct {
+    double nu;            /* kinematic viscosity (lattice units); if <= 0 it is
+                             derived as nu = u_char L_char / Re (Sec. 2.2 Re definition) */
+    double Re;            /* Reynolds number */
+    double u_char;        /* characteristic velocity (throat mean velocity) */
+    double L_char;        /* characteristic length (throat diameter, cells) */
+    double omega3, omega4, omega5, omega6;  /* ghost rates of orders 3..6 (default 1,
+                             Appendix A); 0 < rate < 2 */
+    double u_in;          /* mean inlet velocity u0 (lattice units), |u_in| < 1/sqrt(3) */
+    double d_in;          /* inlet diameter d0 in cells (parabolic profile); <= 0: nx */
+    double axis_x, axis_y;/* nozzle axis position in cell-face coordinates;
+                             negative: box centre nx/2, ny/2 */
+    double noise_amp;     /* relative inlet perturbation: u_b += noise_amp u0 U(-1,1) per component */
+    double rho_out;       /* outlet density (default 1) */
+    uint64_t noise_seed;  /* perturbation seed */
+    int32_t inlet_profile;/* LBM_PROFILE_PLUG or LBM_PROFILE_PARABOLIC */
+    int32_t reserved;
+} lbm_params;
+
+/* Human-readable name of a status code (static string). */
+const char *lbm_status_string(lbm_status s);
+
+/* Defaults: nu = 0, Re = 0 (must be set), ghost rates 1, plug inlet u_in = 0,
+ * d_in = 0 (box width), axis at the box centre, no noise, rho_out = 1. */
+void lbm_params_default(lbm_params *p);
+
+/* Create a context on desc->device bound to desc->stream.  Allocates nothing
+ * on the device until lbm_set_geometry.  *out receives the context.
+ * Errors: LBM_ERR_ARG (bad sizes, precision, scale), LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out);
+
+/* Free every device buffer of ctx (through its allocator) and ctx itself.
+ * Synchronises the stream first.  NULL is accepted. */
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Description of the last error on ctx ("" if none). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Voxelise the axisymmetric FDA-type nozzle of Sec. 2.2 along z into a host
+ * flag array out[L_total][D][D] (x fastest): inlet pipe of diameter D and
+ * length L_in, a cone of half-angle half_angle_deg down to diameter d
+ * (L_cone < 0: its length is round((D - d) / 2 / tan(angle))), a throat of
+ * length L_throat, then diameter D to L_total.  Voxel (x,y,z) is inside iff
+ * (x+1/2-D/2)^2 + (y+1/2-D/2)^2 <= r(z+1/2)^2, the cone radius following the
+ * half-angle and never below d/2.  Inside voxels of plane z = 0 are INLET, of
+ * plane z = L_total-1 OUTLET, other inside voxels FLUID, the rest SOLID.
+ * Errors: LBM_ERR_ARG. */
+lbm_status lbm_make_nozzle(int32_t D, int32_t d, int32_t L_in, int32_t L_cone, int32_t L_throat,
+                           int32_t L_total, double half_angle_deg, uint8_t *out);
+
+/* Install the geometry: flags[nz][ny][nx] host array of LBM_SOLID / FLUID /
+ * INLET / OUTLET (copied).  Builds the fluid-only sparse index (rows of
+ * x-contiguous active cells, per-cell bounce-back link mask) and allocates the
+ * population buffers.  Every INLET/OUTLET cell needs exactly one axis
+ * neighbour that is FLUID (its extrapolation partner).  Resets the step
+ * counter; populations are undefined until an init call.
+ * Errors: LBM_ERR_ARG (bad flag value, inconsistent boundary node, too many
+ * cells), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *flags);
+
+/* Number of active (FLUID + INLET + OUTLET) cells. */
+lbm_status lbm_fluid_count(lbm_ctx *ctx, int64_t *n);
+
+/* Set the flow parameters.  omega = 1/(3 nu + 1/2) (Sec. 2.1).
+ * Errors: LBM_ERR_ARG unless 0 < omega < 2, ghost rates in (0, 2),
+ * |u_in| and u_char below the lattice sound speed 1/sqrt(3). */
+lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p);
+
+/* The relaxation rate omega in use. */
+lbm_status lbm_get_omega(lbm_ctx *ctx, double *omega);
+
+/* f = f^eq(rho, u) on every active cell (uniform state); resets the step
+ * counter and the statistics. */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]);
+
+/* f = f^eq(rho(x), u(x)) from host arrays rho[n], u[n][3] in the given layout. */
+lbm_status lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u, int32_t layout);
+
+/* Set / read the populations f_i (post-collision state at the current time)
+ * from / to a host array f[n][27].  Values are converted to the storage
+ * precision (FP16S rounds (f - w) s to nearest even). */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int32_t layout);
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int32_t layout);
+
+/* Enqueue n >= 0 time steps on the context stream (asynchronous).  Each step
+ * is one fused stream-collide kernel (with the boundary nodes folded in); the
+ * health check and the statistics sampling ride on the same kernel when due.
+ * Errors: LBM_ERR_STATE (no geometry / params / init), LBM_ERR_CUDA. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Wait for the stream; report a deferred LBM_ERR_UNSTABLE (a health check saw
+ * a non-finite value) or LBM_ERR_CUDA.  The unstable flag stays set until the
+ * next init call. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Number of steps taken since the last init. */
+lbm_status lbm_step_count(lbm_ctx *ctx, int64_t *t);
+
+/* Every k >= 1 steps, fold the health check (FP64 mass, momentum, non-finite
+ * count, max |u|) into the step kernel; k = 0 disables it (default). */
+lbm_status lbm_set_check_every(lbm_ctx *ctx, int64_t k);
+
+/* Density and velocity of every active cell (moments of the current state;
+ * equal to the pre-collision moments by conservation): rho[n], u[n][3]. */
+lbm_status lbm_get_moments(lbm_ctx *ctx, double *rho, double *u, int32_t layout);
+
+/* FP64 totals over active cells: mass = sum rho, mom = sum rho u, computed
+ * on the device by a deterministic fixed-order reduction (Sec. 2.1 moments). */
+lbm_status lbm_get_totals(lbm_ctx *ctx, double *mass, double mom[3]);
+
+/* Health record of the last check (check_every or lbm_get_totals):
+ * out[0] mass, out[1..3] momentum, out[4] max |u|, out[5] non-finite count. */
+lbm_status lbm_get_health(lbm_ctx *ctx, double out[6]);
+
+/* Time averages (Sec. 2.2, mean/fluctuation decomposition and Reynolds
+ * stress): from the next step on, every stride-th step adds u_z and u_z^2 of
+ * every active cell to FP64 accumulators.  lbm_stats_end stops sampling. */
+lbm_status lbm_stats_begin(lbm_ctx *ctx, int64_t stride);
+lbm_status lbm_stats_end(lbm_ctx *ctx);
+lbm_status lbm_stats_reset(lbm_ctx *ctx);
+
+/* Means over the samples: mean_uz[n] = <u_z>, mean_uzuz[n] = <u_z^2> (either
+ * may be NULL), and the sample count.  RMS = sqrt(<u_z^2> - <u_z>^2); the
+ * axial Reynolds normal stress is rho (<u_z^2> - <u_z>^2). */
+lbm_status lbm_stats_get(lbm_ctx *ctx, double *mean_uz, double *mean_uzuz, int64_t *n_samples,
+                         int32_t layout);
+
+/* Checkpoint: the current populations (native storage precision, bitwise),
+ * the step counter and the statistics accumulators.  lbm_restore needs a
+ * context with the same geometry, precision and scale. */
+lbm_status lbm_checkpoint_size(lbm_ctx *ctx, size_t *bytes);
+lbm_status lbm_checkpoint(lbm_ctx *ctx, void *buf, size_t bytes);
+lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* Layout facts for measurement: number of storage slots (active cells plus
+ * row padding), bytes of one population buffer, device bytes held. */
+lbm_status lbm_layout_info(lbm_ctx *ctx, int64_t *slots, int64_t *buffer_bytes, int64_t *device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,713 @@
+// C ABI of the lattice Boltzmann library (declared in include/lbm.h): context
+// management, device memory, parameter derivation, and the step loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_desc desc{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool has_geom = false, has_params = false, has_state = false;
+    HostIndex idx;
+    // device buffers
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint32_t *d_mask = nullptr;
+    int32_t *d_row_base = nullptr;
+    int2 *d_chunks = nullptr;
+    int32_t *d_slot_of_active = nullptr;
+    double *d_partials = nullptr;
+    double *d_health = nullptr;
+    uint32_t *d_status = nullptr;
+    double *d_stats = nullptr;
+    int nblocks = 0;
+    int64_t device_bytes = 0;
+    // parameters and state
+    lbm_params params{};
+    double omega = 0.0;
+    bool ghost1 = true;
+    int64_t t = 0;
+    int64_t check_every = 0;
+    bool stats_on = false;
+    int64_t stats_stride = 1, stats_start = 0, stats_samples = 0;
+    double health[6] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+int storage_bytes(int precision) { return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2); }
+
+void *dev_alloc(lbm_ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (c->desc.allocator.alloc) {
+        p = c->desc.allocator.alloc(bytes, c->desc.allocator.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->device_bytes += (int64_t)bytes;
+    return p;
+}
+
+void dev_free(lbm_ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    c->device_bytes -= (int64_t)bytes;
+    if (c->desc.allocator.alloc)
+        c->desc.allocator.free(p, c->desc.allocator.user);
+    else
+        cudaFree(p);
+}
+
+size_t pop_bytes(const lbm_ctx *c) { return (size_t)27 * (size_t)c->idx.nslots * storage_bytes(c->desc.precision); }
+
+void release_geometry(lbm_ctx *c) {
+    const size_t ns = (size_t)c->idx.nslots;
+    dev_free(c, c->f[0], pop_bytes(c));
+    dev_free(c, c->f[1], pop_bytes(c));
+    dev_free(c, c->d_mask, ns * 4);
+    dev_free(c, c->d_row_base, c->idx.row_base.size() * 4);
+    dev_free(c, c->d_chunks, c->idx.chunks.size() * 8);
+    dev_free(c, c->d_slot_of_active, c->idx.slot_of_active.size() * 4);
+    dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
+    dev_free(c, c->d_health, 8 * 8);
+    dev_free(c, c->d_status, 256);
+    dev_free(c, c->d_stats, 2 * ns * 8);
+    c->f[0] = c->f[1] = nullptr;
+    c->d_mask = nullptr;
+    c->d_row_base = nullptr;
+    c->d_chunks = nullptr;
+    c->d_slot_of_active = nullptr;
+    c->d_partials = nullptr;
+    c->d_health = nullptr;
+    c->d_status = nullptr;
+    c->d_stats = nullptr;
+    c->has_geom = c->has_state = false;
+}
+
+float fp16_scale(const lbm_ctx *c) { return c->desc.precision == LBM_FP16S ? c->desc.fp16_scale : 1.0f; }
+
+// Dispatch a launcher over the storage precision.
+#define DISPATCH(prec, fn, ...)                                   \
+    ((prec) == LBM_FP64 ? fn<0>(__VA_ARGS__)                      \
+                        : ((prec) == LBM_FP32 ? fn<1>(__VA_ARGS__) : fn<2>(__VA_ARGS__)))
+
+// Host arrays <-> active order.
+int64_t layout_count(const lbm_ctx *c, int32_t layout) {
+    return layout == LBM_LAYOUT_BOX ? (int64_t)c->desc.nx * c->desc.ny * c->desc.nz : c->idx.n_active;
+}
+
+template <class F>
+void for_active(const lbm_ctx *c, int32_t layout, F fn) {  // fn(active k, host row)
+    for (int64_t k = 0; k < c->idx.n_active; ++k) fn(k, layout == LBM_LAYOUT_BOX ? c->idx.box_of_active[k] : k);
+}
+
+lbm_status need(lbm_ctx *c, bool geom, bool params, bool state) {
+    if (!c) return LBM_ERR_ARG;
+    if (geom && !c->has_geom) return fail(c, LBM_ERR_STATE, "no geometry: call lbm_set_geometry first");
+    if (params && !c->has_params) return fail(c, LBM_ERR_STATE, "no parameters: call lbm_set_params first");
+    if (state && !c->has_state) return fail(c, LBM_ERR_STATE, "no state: call an init function first");
+    c->err.clear();
+    return LBM_OK;
+}
+
+lbm_status reset_state(lbm_ctx *c) {
+    c->t = 0;
+    c->stats_samples = 0;
+    c->stats_on = false;
+    CK(cudaMemsetAsync(c->d_status, 0, 4, c->stream), "reset status");
+    if (c->d_stats) CK(cudaMemsetAsync(c->d_stats, 0, 2 * (size_t)c->idx.nslots * 8, c->stream), "reset stats");
+    c->has_state = true;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_OOM: return "out of device memory";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_STATE: return "call out of order";
+        case LBM_ERR_UNSTABLE: return "non-finite state";
+        case LBM_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+void lbm_params_default(lbm_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->omega3 = p->omega4 = p->omega5 = p->omega6 = 1.0;
+    p->inlet_profile = LBM_PROFILE_PLUG;
+    p->axis_x = p->axis_y = -1.0;
+    p->rho_out = 1.0;
+}
+
+lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out) {
+    if (!desc || !out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1) return LBM_ERR_ARG;
+    if ((int64_t)desc->nx * desc->ny * desc->nz > ((int64_t)1 << 40)) return LBM_ERR_ARG;
+    if (desc->precision < LBM_FP64 || desc->precision > LBM_FP16S) return LBM_ERR_ARG;
+    if (desc->periodic & ~7) return LBM_ERR_ARG;
+    if ((desc->allocator.alloc == nullptr) != (desc->allocator.free == nullptr)) return LBM_ERR_ARG;
+    float s = desc->fp16_scale == 0.0f ? 4096.0f : desc->fp16_scale;
+    int ex;
+    if (!(s > 0.0f) || std::frexp(s, &ex) != 0.5f) return LBM_ERR_ARG;  // power of two
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    if (desc->device < 0 || desc->device >= ndev) return LBM_ERR_ARG;
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_OOM;
+    c->desc = *desc;
+    c->desc.fp16_scale = s;
+    c->stream = static_cast<cudaStream_t>(desc->stream);
+    lbm_params_default(&c->params);
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx *c) {
+    if (!c) return LBM_OK;
+    DeviceGuard g(c->desc.device);
+    cudaStreamSynchronize(c->stream);
+    release_geometry(c);
+    delete c;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
+    if (!c) return LBM_ERR_ARG;
+    if (!flags) return fail(c, LBM_ERR_ARG, "flags is NULL");
+    DeviceGuard g(c->desc.device);
+    HostIndex idx;
+    std::string msg = build_index(flags, c->desc.nx, c->desc.ny, c->desc.nz, c->desc.periodic, idx);
+    if (!msg.empty()) return fail(c, LBM_ERR_ARG, msg);
+    CK(cudaStreamSynchronize(c->stream), "sync before geometry change");
+    release_geometry(c);
+    c->idx = std::move(idx);
+    const size_t ns = (size_t)c->idx.nslots;
+    c->nblocks = reduce_blocks((int32_t)c->idx.chunks.size());
+    c->f[0] = dev_alloc(c, pop_bytes(c));
+    c->f[1] = dev_alloc(c, pop_bytes(c));
+    c->d_mask = (uint32_t *)dev_alloc(c, ns * 4);
+    c->d_row_base = (int32_t *)dev_alloc(c, c->idx.row_base.size() * 4);
+    c->d_chunks = (int2 *)dev_alloc(c, c->idx.chunks.size() * 8);
+    c->d_slot_of_active = (int32_t *)dev_alloc(c, c->idx.slot_of_active.size() * 4);
+    c->d_partials = (double *)dev_alloc(c, (size_t)c->nblocks * REDUCE_SLOTS * 8);
+    c->d_health = (double *)dev_alloc(c, 8 * 8);
+    c->d_status = (uint32_t *)dev_alloc(c, 256);
+    if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_base || !c->d_chunks || !c->d_slot_of_active ||
+        !c->d_partials || !c->d_health || !c->d_status) {
+        release_geometry(c);
+        return fail(c, LBM_ERR_OOM, "device allocation failed in lbm_set_geometry");
+    }
+    CK(cudaMemcpyAsync(c->d_mask, c->idx.mask.data(), ns * 4, cudaMemcpyHostToDevice, c->stream), "copy mask");
+    CK(cudaMemcpyAsync(c->d_row_base, c->idx.row_base.data(), c->idx.row_base.size() * 4, cudaMemcpyHostToDevice,
+                       c->stream),
+       "copy row_base");
+    CK(cudaMemcpyAsync(c->d_chunks, c->idx.chunks.data(), c->idx.chunks.size() * 8, cudaMemcpyHostToDevice,
+                       c->stream),
+       "copy chunks");
+    CK(cudaMemcpyAsync(c->d_slot_of_active, c->idx.slot_of_active.data(), c->idx.slot_of_active.size() * 4,
+                       cudaMemcpyHostToDevice, c->stream),
+       "copy slot map");
+    // Padding slots are never read by the step kernel; zero both buffers so
+    // that checkpoints and dumps are deterministic.
+    CK(cudaMemsetAsync(c->f[0], 0, pop_bytes(c), c->stream), "clear f0");
+    CK(cudaMemsetAsync(c->f[1], 0, pop_bytes(c), c->stream), "clear f1");
+    CK(cudaMemsetAsync(c->d_status, 0, 4, c->stream), "clear status");
+    CK(cudaStreamSynchronize(c->stream), "sync geometry upload");
+    c->has_geom = true;
+    c->has_state = false;
+    c->cur = 0;
+    c->t = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_fluid_count(lbm_ctx *c, int64_t *n) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (!n) return fail(c, LBM_ERR_ARG, "NULL output");
+    *n = c->idx.n_active;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_params(lbm_ctx *c, const lbm_params *p) {
+    if (!c) return LBM_ERR_ARG;
+    if (!p) return fail(c, LBM_ERR_ARG, "params is NULL");
+    double nu = p->nu;
+    if (!(nu > 0.0)) {
+        if (!(p->Re > 0.0) || !(p->L_char > 0.0) || !(std::fabs(p->u_char) > 0.0))
+            return fail(c, LBM_ERR_ARG, "give nu > 0, or Re, u_char and L_char > 0");
+        nu = std::fabs(p->u_char) * p->L_char / p->Re;  // Re = u L / nu (Sec. 2.2)
+    }
+    const double omega = 1.0 / (3.0 * nu + 0.5);      // tau = nu / theta0 + 1/2 (Sec. 2.1)
+    if (!(omega > 0.0 && omega < 2.0)) return fail(c, LBM_ERR_ARG, "omega outside (0, 2)");
+    const double g[4] = {p->omega3, p->omega4, p->omega5, p->omega6};
+    for (double r : g)
+        if (!(r > 0.0 && r < 2.0)) return fail(c, LBM_ERR_ARG, "ghost rates must lie in (0, 2)");
+    const double cs = 1.0 / std::sqrt(3.0);
+    if (!(std::fabs(p->u_in) < cs) || !(std::fabs(p->u_char) < cs))
+        return fail(c, LBM_ERR_ARG, "velocities must stay below the lattice sound speed");
+    if (p->inlet_profile != LBM_PROFILE_PLUG && p->inlet_profile != LBM_PROFILE_PARABOLIC)
+        return fail(c, LBM_ERR_ARG, "unknown inlet profile");
+    if (!(p->noise_amp >= 0.0) || !(p->rho_out > 0.0)) return fail(c, LBM_ERR_ARG, "bad noise or rho_out");
+    c->params = *p;
+    c->params.nu = nu;
+    if (!(c->params.d_in > 0.0)) c->params.d_in = c->desc.nx;
+    if (c->params.axis_x < 0.0) c->params.axis_x = c->desc.nx / 2.0;
+    if (c->params.axis_y < 0.0) c->params.axis_y = c->desc.ny / 2.0;
+    c->omega = omega;
+    c->ghost1 = g[0] == 1.0 && g[1] == 1.0 && g[2] == 1.0 && g[3] == 1.0;
+    c->has_params = true;
+    c->err.clear();
+    return LBM_OK;
+}
+
+lbm_status lbm_get_omega(lbm_ctx *c, double *omega) {
+    lbm_status st = need(c, false, true, false);
+    if (st) return st;
+    if (!omega) return fail(c, LBM_ERR_ARG, "NULL output");
+    *omega = c->omega;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *c, double rho, const double u[3]) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (!u || !(rho > 0.0)) return fail(c, LBM_ERR_ARG, "need rho > 0 and u");
+    DeviceGuard g(c->desc.device);
+    c->cur = 0;
+    CK(DISPATCH(c->desc.precision, launch_init_eq, c->f[0], c->d_slot_of_active, c->idx.n_active, c->idx.nslots,
+                fp16_scale(c), nullptr, nullptr, rho, u[0], u[1], u[2], c->stream),
+       "init equilibrium");
+    st = reset_state(c);
+    if (st) return st;
+    CK(cudaStreamSynchronize(c->stream), "sync init");
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx *c, const double *rho, const double *u, int32_t layout) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (!rho || !u || (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX))
+        return fail(c, LBM_ERR_ARG, "need rho, u and a valid layout");
+    DeviceGuard g(c->desc.device);
+    const int64_t n = c->idx.n_active;
+    std::vector<double> h((size_t)n * 4);
+    for_active(c, layout, [&](int64_t k, int64_t r) {
+        h[(size_t)k] = rho[r];
+        for (int a = 0; a < 3; ++a) h[(size_t)n + 3 * (size_t)k + a] = u[3 * r + a];
+    });
+    double *d = (double *)dev_alloc(c, (size_t)n * 4 * 8);
+    if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), (size_t)n * 4 * 8, cudaMemcpyHostToDevice, c->stream);
+    c->cur = 0;
+    if (e == cudaSuccess)
+        e = DISPATCH(c->desc.precision, launch_init_eq, c->f[0], c->d_slot_of_active, n, c->idx.nslots,
+                     fp16_scale(c), d, d + n, 1.0, 0.0, 0.0, 0.0, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, d, (size_t)n * 4 * 8);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init fields");
+    return reset_state(c);
+}
+
+lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t layout) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (!f || (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX))
+        return fail(c, LBM_ERR_ARG, "need f and a valid layout");
+    DeviceGuard g(c->desc.device);
+    const int64_t n = c->idx.n_active;
+    const size_t bytes = (size_t)n * 27 * 8;
+    double *d = (double *)dev_alloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
+    cudaError_t e = cudaSuccess;
+    if (layout == LBM_LAYOUT_ACTIVE) {
+        e = cudaMemcpyAsync(d, f, bytes, cudaMemcpyHostToDevice, c->stream);
+    } else {
+        std::vector<double> h((size_t)n * 27);
+        for_active(c, layout, [&](int64_t k, int64_t r) { memcpy(&h[27 * (size_t)k], f + 27 * r, 27 * 8); });
+        e = cudaMemcpyAsync(d, h.data(), bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    c->cur = 0;
+    if (e == cudaSuccess)
+        e = DISPATCH(c->desc.precision, launch_set_populations, c->f[0], c->d_slot_of_active, n, c->idx.nslots,
+                     fp16_scale(c), d, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, d, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set populations");
+    return reset_state(c);
+}
+
+lbm_status lbm_get_populations(lbm_ctx *c, double *f, int32_t layout) {
+    lbm_status st = need(c, true, false, true);
+    if (st) return st;
+    if (!f || (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX))
+        return fail(c, LBM_ERR_ARG, "need f and a valid layout");
+    DeviceGuard g(c->desc.device);
+    const int64_t n = c->idx.n_active;
+    const size_t bytes = (size_t)n * 27 * 8;
+    double *d = (double *)dev_alloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
+    cudaError_t e = DISPATCH(c->desc.precision, launch_get_populations, c->f[c->cur], c->d_slot_of_active, n,
+                             c->idx.nslots, 1.0f / fp16_scale(c), d, c->stream);
+    if (layout == LBM_LAYOUT_ACTIVE) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    } else {
+        std::vector<double> h((size_t)n * 27);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) {
+            memset(f, 0, (size_t)layout_count(c, layout) * 27 * 8);
+            for_active(c, layout, [&](int64_t k, int64_t r) { memcpy(f + 27 * r, &h[27 * (size_t)k], 27 * 8); });
+        }
+    }
+    dev_free(c, d, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get populations");
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int64_t n) {
+    lbm_status st = need(c, true, true, true);
+    if (st) return st;
+    if (n < 0) return fail(c, LBM_ERR_ARG, "negative step count");
+    DeviceGuard g(c->desc.device);
+    StepArgs a{};
+    a.mask = c->d_mask;
+    a.row_base = c->d_row_base;
+    a.chunks = c->d_chunks;
+    a.stride = c->idx.nslots;
+    a.nchunks = (int32_t)c->idx.chunks.size();
+    a.nx = c->desc.nx;
+    a.ny = c->desc.ny;
+    a.nz = c->desc.nz;
+    a.profile = c->params.inlet_profile;
+    a.omega = c->omega;
+    a.ghost[0] = c->params.omega3;
+    a.ghost[1] = c->params.omega4;
+    a.ghost[2] = c->params.omega5;
+    a.ghost[3] = c->params.omega6;
+    a.u_in = c->params.u_in;
+    a.d_in = c->params.d_in;
+    a.axis_x = c->params.axis_x;
+    a.axis_y = c->params.axis_y;
+    a.noise_amp = c->params.noise_amp;
+    a.rho_out = c->params.rho_out;
+    a.seed = c->params.noise_seed;
+    a.scale = fp16_scale(c);
+    a.inv_scale = 1.0f / a.scale;
+    a.stats = c->d_stats;
+    a.partials = c->d_partials;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t t_new = c->t + 1;
+        a.fin = c->f[c->cur];
+        a.fout = c->f[1 - c->cur];
+        a.t_new = t_new;
+        a.flags = 0;
+        const bool check = c->check_every > 0 && t_new % c->check_every == 0;
+        if (check) a.flags |= STEP_REDUCE;
+        if (c->stats_on && t_new >= c->stats_start && (t_new - c->stats_start) % c->stats_stride == 0) {
+            a.flags |= STEP_STATS;
+            ++c->stats_samples;
+        }
+        CK(DISPATCH(c->desc.precision, launch_step, a, c->ghost1, c->stream), "step kernel");
+        if (check) CK(launch_finalize(c->d_partials, c->nblocks, c->d_health, c->d_status, c->stream), "finalize");
+        c->cur = 1 - c->cur;
+        c->t = t_new;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx *c) {
+    if (!c) return LBM_ERR_ARG;
+    DeviceGuard g(c->desc.device);
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (!c->has_geom) return LBM_OK;
+    uint32_t status = 0;
+    CK(cudaMemcpyAsync(&status, c->d_status, 4, cudaMemcpyDeviceToHost, c->stream), "read status");
+    CK(cudaStreamSynchronize(c->stream), "sync status");
+    if (c->check_every > 0) {
+        CK(cudaMemcpyAsync(c->health, c->d_health, 6 * 8, cudaMemcpyDeviceToHost, c->stream), "read health");
+        CK(cudaStreamSynchronize(c->stream), "sync health");
+    }
+    if (status & 1u) return fail(c, LBM_ERR_UNSTABLE, "a health check found non-finite populations");
+    return LBM_OK;
+}
+
+lbm_status lbm_step_count(lbm_ctx *c, int64_t *t) {
+    if (!c || !t) return LBM_ERR_ARG;
+    *t = c->t;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_check_every(lbm_ctx *c, int64_t k) {
+    if (!c) return LBM_ERR_ARG;
+    if (k < 0) return fail(c, LBM_ERR_ARG, "negative check interval");
+    c->check_every = k;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_moments(lbm_ctx *c, double *rho, double *u, int32_t layout) {
+    lbm_status st = need(c, true, false, true);
+    if (st) return st;
+    if ((!rho && !u) || (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX))
+        return fail(c, LBM_ERR_ARG, "need an output array and a valid layout");
+    DeviceGuard g(c->desc.device);
+    const int64_t n = c->idx.n_active;
+    const size_t bytes = (size_t)n * 4 * 8;
+    double *d = (double *)dev_alloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
+    std::vector<double> h((size_t)n * 4);
+    cudaError_t e = DISPATCH(c->desc.precision, launch_moments, c->f[c->cur], c->d_slot_of_active, n, c->idx.nslots,
+                             1.0f / fp16_scale(c), d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, d, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get moments");
+    const int64_t total = layout_count(c, layout);
+    if (rho) memset(rho, 0, (size_t)total * 8);
+    if (u) memset(u, 0, (size_t)total * 3 * 8);
+    for_active(c, layout, [&](int64_t k, int64_t r) {
+        if (rho) rho[r] = h[4 * (size_t)k];
+        if (u)
+            for (int a = 0; a < 3; ++a) u[3 * r + a] = h[4 * (size_t)k + 1 + a];
+    });
+    return LBM_OK;
+}
+
+lbm_status lbm_get_totals(lbm_ctx *c, double *mass, double mom[3]) {
+    lbm_status st = need(c, true, false, true);
+    if (st) return st;
+    DeviceGuard g(c->desc.device);
+    CK(DISPATCH(c->desc.precision, launch_reduce, c->f[c->cur], c->d_mask, c->d_chunks, c->d_row_base,
+                (int32_t)c->idx.chunks.size(), c->idx.nslots, 1.0f / fp16_scale(c), c->d_partials, c->stream),
+       "reduce");
+    CK(launch_finalize(c->d_partials, c->nblocks, c->d_health, c->d_status, c->stream), "finalize");
+    CK(cudaMemcpyAsync(c->health, c->d_health, 6 * 8, cudaMemcpyDeviceToHost, c->stream), "read totals");
+    CK(cudaStreamSynchronize(c->stream), "sync totals");
+    if (mass) *mass = c->health[0];
+    if (mom)
+        for (int a = 0; a < 3; ++a) mom[a] = c->health[1 + a];
+    return LBM_OK;
+}
+
+lbm_status lbm_get_health(lbm_ctx *c, double out[6]) {
+    if (!c || !out) return LBM_ERR_ARG;
+    for (int k = 0; k < 6; ++k) out[k] = c->health[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_stats_begin(lbm_ctx *c, int64_t stride) {
+    lbm_status st = need(c, true, false, true);
+    if (st) return st;
+    if (stride < 1) return fail(c, LBM_ERR_ARG, "stride must be >= 1");
+    DeviceGuard g(c->desc.device);
+    if (!c->d_stats) {
+        c->d_stats = (double *)dev_alloc(c, 2 * (size_t)c->idx.nslots * 8);
+        if (!c->d_stats) return fail(c, LBM_ERR_OOM, "statistics allocation failed");
+        CK(cudaMemsetAsync(c->d_stats, 0, 2 * (size_t)c->idx.nslots * 8, c->stream), "clear stats");
+        c->stats_samples = 0;
+    }
+    c->stats_on = true;
+    c->stats_stride = stride;
+    c->stats_start = c->t + 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_stats_end(lbm_ctx *c) {
+    if (!c) return LBM_ERR_ARG;
+    c->stats_on = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_stats_reset(lbm_ctx *c) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    DeviceGuard g(c->desc.device);
+    if (c->d_stats) CK(cudaMemsetAsync(c->d_stats, 0, 2 * (size_t)c->idx.nslots * 8, c->stream), "clear stats");
+    c->stats_samples = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_stats_get(lbm_ctx *c, double *mean_uz, double *mean_uzuz, int64_t *n_samples, int32_t layout) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX) return fail(c, LBM_ERR_ARG, "bad layout");
+    if (n_samples) *n_samples = c->stats_samples;
+    if (!mean_uz && !mean_uzuz) return LBM_OK;
+    const int64_t n = c->idx.n_active;
+    const int64_t total = layout_count(c, layout);
+    if (mean_uz) memset(mean_uz, 0, (size_t)total * 8);
+    if (mean_uzuz) memset(mean_uzuz, 0, (size_t)total * 8);
+    if (!c->d_stats || c->stats_samples == 0) return LBM_OK;
+    DeviceGuard g(c->desc.device);
+    const size_t bytes = (size_t)n * 2 * 8;
+    double *d = (double *)dev_alloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
+    std::vector<double> h((size_t)n * 2);
+    cudaError_t e = launch_stats_mean(c->d_stats, c->d_slot_of_active, n, c->idx.nslots,
+                                      1.0 / (double)c->stats_samples, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, d, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stats readback");
+    for_active(c, layout, [&](int64_t k, int64_t r) {
+        if (mean_uz) mean_uz[r] = h[2 * (size_t)k];
+        if (mean_uzuz) mean_uzuz[r] = h[2 * (size_t)k + 1];
+    });
+    return LBM_OK;
+}
+
+// Checkpoint image: header, then the current population buffer (native
+// storage, bitwise), then the two statistics accumulators if allocated.
+struct CkptHeader {
+    uint64_t magic;
+    int32_t version, precision, nx, ny, nz, periodic;
+    float scale;
+    int32_t has_stats;
+    int64_t nslots, n_active, t, stats_samples, stats_stride, stats_start;
+    int32_t stats_on, reserved;
+};
+static const uint64_t CKPT_MAGIC = 0x4c424d3237434b50ULL;  // "LBM27CKP"
+
+lbm_status lbm_checkpoint_size(lbm_ctx *c, size_t *bytes) {
+    lbm_status st = need(c, true, false, true);
+    if (st) return st;
+    if (!bytes) return fail(c, LBM_ERR_ARG, "NULL output");
+    *bytes = sizeof(CkptHeader) + pop_bytes(c) + (c->d_stats ? 2 * (size_t)c->idx.nslots * 8 : 0);
+    return LBM_OK;
+}
+
+lbm_status lbm_checkpoint(lbm_ctx *c, void *buf, size_t bytes) {
+    size_t need_bytes = 0;
+    lbm_status st = lbm_checkpoint_size(c, &need_bytes);
+    if (st) return st;
+    if (!buf || bytes < need_bytes) return fail(c, LBM_ERR_ARG, "checkpoint buffer too small");
+    DeviceGuard g(c->desc.device);
+    CkptHeader h{};
+    h.magic = CKPT_MAGIC;
+    h.version = 1;
+    h.precision = c->desc.precision;
+    h.nx = c->desc.nx;
+    h.ny = c->desc.ny;
+    h.nz = c->desc.nz;
+    h.periodic = c->desc.periodic;
+    h.scale = fp16_scale(c);
+    h.has_stats = c->d_stats != nullptr;
+    h.nslots = c->idx.nslots;
+    h.n_active = c->idx.n_active;
+    h.t = c->t;
+    h.stats_samples = c->stats_samples;
+    h.stats_stride = c->stats_stride;
+    h.stats_start = c->stats_start;
+    h.stats_on = c->stats_on;
+    char *p = static_cast<char *>(buf);
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    CK(cudaMemcpyAsync(p, c->f[c->cur], pop_bytes(c), cudaMemcpyDeviceToHost, c->stream), "checkpoint f");
+    p += pop_bytes(c);
+    if (c->d_stats)
+        CK(cudaMemcpyAsync(p, c->d_stats, 2 * (size_t)c->idx.nslots * 8, cudaMemcpyDeviceToHost, c->stream),
+           "checkpoint stats");
+    CK(cudaStreamSynchronize(c->stream), "sync checkpoint");
+    return LBM_OK;
+}
+
+lbm_status lbm_restore(lbm_ctx *c, const void *buf, size_t bytes) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (!buf || bytes < sizeof(CkptHeader)) return fail(c, LBM_ERR_ARG, "checkpoint too small");
+    CkptHeader h;
+    memcpy(&h, buf, sizeof h);
+    if (h.magic != CKPT_MAGIC || h.version != 1) return fail(c, LBM_ERR_ARG, "not a checkpoint image");
+    if (h.precision != c->desc.precision || h.nx != c->desc.nx || h.ny != c->desc.ny || h.nz != c->desc.nz ||
+        h.periodic != c->desc.periodic || h.scale != fp16_scale(c) || h.nslots != c->idx.nslots ||
+        h.n_active != c->idx.n_active)
+        return fail(c, LBM_ERR_ARG, "checkpoint does not match this context's geometry or precision");
+    const size_t need_bytes = sizeof h + pop_bytes(c) + (h.has_stats ? 2 * (size_t)h.nslots * 8 : 0);
+    if (bytes < need_bytes) return fail(c, LBM_ERR_ARG, "checkpoint truncated");
+    DeviceGuard g(c->desc.device);
+    const char *p = static_cast<const char *>(buf) + sizeof h;
+    c->cur = 0;
+    CK(cudaMemcpyAsync(c->f[0], p, pop_bytes(c), cudaMemcpyHostToDevice, c->stream), "restore f");
+    p += pop_bytes(c);
+    if (h.has_stats) {
+        if (!c->d_stats) {
+            c->d_stats = (double *)dev_alloc(c, 2 * (size_t)c->idx.nslots * 8);
+            if (!c->d_stats) return fail(c, LBM_ERR_OOM, "statistics allocation failed");
+        }
+        CK(cudaMemcpyAsync(c->d_stats, p, 2 * (size_t)h.nslots * 8, cudaMemcpyHostToDevice, c->stream),
+           "restore stats");
+    }
+    CK(cudaMemsetAsync(c->d_status, 0, 4, c->stream), "reset status");
+    CK(cudaStreamSynchronize(c->stream), "sync restore");
+    c->t = h.t;
+    c->stats_samples = h.stats_samples;
+    c->stats_stride = h.stats_stride;
+    c->stats_start = h.stats_start;
+    c->stats_on = h.stats_on != 0 && h.has_stats;
+    c->has_state = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_layout_info(lbm_ctx *c, int64_t *slots, int64_t *buffer_bytes, int64_t *device_bytes) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (slots) *slots = c->idx.nslots;
+    if (buffer_bytes) *buffer_bytes = (int64_t)pop_bytes(c);
+    if (device_bytes) *device_bytes = c->device_bytes;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every
+function include/lbm.h declares, and its host-only entry points behave."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2204_10566_gb300 import build as lbuild
+from paper_2204_10566_gb300 import inputs as I
+from paper_2204_10566_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lbuild.build()
+    return lbm.capi()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(lib):
+    names = header_functions()
+    assert len(names) >= 29
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lbm.declared_functions()) == names
+
+
+def test_status_strings(lib):
+    assert lib.lbm_status_string(0) == b"ok"
+    assert lib.lbm_status_string(5) == b"non-finite state"
+
+
+def test_params_default(lib):
+    p = lbm.lbm_params()
+    lib.lbm_params_default(C.byref(p))
+    assert (p.omega3, p.omega4, p.omega5, p.omega6) == (1.0, 1.0, 1.0, 1.0)
+    assert p.rho_out == 1.0 and p.inlet_profile == lbm.LBM_PROFILE_PLUG and p.axis_x < 0
+
+
+def test_struct_sizes_match_header():
+    # lbm_desc: 7 int32 + float, pointer, 3 pointers; lbm_params: 14 doubles + u64 + 2 int32
+    assert C.sizeof(lbm.lbm_desc) == 32 + 8 + 24
+    assert C.sizeof(lbm.lbm_params) == 14 * 8 + 8 + 8
+
+
+@pytest.mark.parametrize("name", ["nozzle_re500_24x24x160", "nozzle_re3500_96x96x800"])
+def test_make_nozzle_matches_input_generator(lib, name):
+    w = I.WORKLOADS[name]
+    got = lbm.make_nozzle(w["D"], w["d"], w["L_total"])
+    assert np.array_equal(got, I.workload_flags(name))
+
+
+def test_make_nozzle_rejects_bad_sizes(lib):
+    out = np.zeros(10, dtype=np.uint8)
+    assert lib.lbm_make_nozzle(8, 12, 8, -1, 4, 10, 10.0, out.ctypes.data) == lbm.LBM_ERR_ARG
+    assert lib.lbm_make_nozzle(8, 4, 8, -1, 4, 10, 95.0, out.ctypes.data) == lbm.LBM_ERR_ARG
+
+
+def test_create_rejects_bad_descriptors(lib):
+    ctx = C.c_void_p()
+    d = lbm.lbm_desc()
+    d.nx, d.ny, d.nz, d.precision = 0, 4, 4, 1
+    assert lib.lbm_create(C.byref(d), C.byref(ctx)) == lbm.LBM_ERR_ARG
+    d.nx, d.precision = 4, 7
+    assert lib.lbm_create(C.byref(d), C.byref(ctx)) == lbm.LBM_ERR_ARG
+    d.precision, d.fp16_scale = 2, 3.0   # not a power of two
+    assert lib.lbm_create(C.byref(d), C.byref(ctx)) == lbm.LBM_ERR_ARG
+    assert lib.lbm_destroy(None) == lbm.LBM_OK
