@@ -142,6 +142,17 @@ const char *lbm_last_error(const lbm_ctx *ctx);
 lbm_status lbm_make_nozzle(int32_t D, int32_t d, int32_t L_in, int32_t L_cone, int32_t L_throat,
                            int32_t L_total, double half_angle_deg, uint8_t *out);
 
+/* Host-only check of a flag field (no device needed): builds the sparse index
+ * exactly as lbm_set_geometry would and re-verifies, independently, the
+ * invariants the kernels rely on (every staged copy 16-byte aligned and inside
+ * its buffer, every fluid cell in exactly one work unit, every pull slot
+ * stored).  out (may be NULL) receives: active cells, storage slots, fluid
+ * segments, fluid chunks, inlet/outlet nodes, wall links, rows, 0.
+ * Errors: LBM_ERR_ARG (inconsistent flag field, same rules as
+ * lbm_set_geometry), LBM_ERR_STATE (an index invariant does not hold). */
+lbm_status lbm_check_layout(const uint8_t *flags, int32_t nx, int32_t ny, int32_t nz, int32_t periodic,
+                            int64_t out[8]);
+
 /* Install the geometry: flags[nz][ny][nx] host array of LBM_SOLID / FLUID /
  * INLET / OUTLET (copied).  Builds the fluid-only sparse index (rows of
  * x-contiguous active cells, per-cell bounce-back link mask) and allocates the

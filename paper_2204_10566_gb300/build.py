@@ -67,5 +67,7 @@ def build(force=False, verbose=False, extra=()):
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else ()))
+    extra = [a for a in sys.argv[1:] if a.startswith("-D")]
+    if "--ptxas" in sys.argv:
+        extra += ["-Xptxas", "-v"]
+    print(build(force="--force" in sys.argv or bool(extra), verbose="-v" in sys.argv, extra=extra))

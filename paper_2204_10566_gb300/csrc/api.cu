@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -20,17 +21,23 @@ struct lbm_ctx {
     bool has_geom = false, has_params = false, has_state = false;
     HostIndex idx;
     // device buffers
-    void *f[2] = {nullptr, nullptr};
+    void *f[2] = {nullptr, nullptr};      // population buffers (inside the raw allocations)
+    void *f_raw[2] = {nullptr, nullptr};
     int cur = 0;
-    uint32_t *d_mask = nullptr;
-    int32_t *d_row_base = nullptr;
+    uint32_t *d_mask = nullptr;           // link words (inside d_mask_raw)
+    uint32_t *d_mask_raw = nullptr;
+    int4 *d_segs = nullptr;
+    int4 *d_row_nb = nullptr;
     int2 *d_chunks = nullptr;
+    int4 *d_bnodes = nullptr;
     int32_t *d_slot_of_active = nullptr;
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
     double *d_stats = nullptr;
-    int nblocks = 0;
+    int nblocks = 0;        // partial-sum capacity (blocks)
+    int step_blocks = 0;    // blocks of one step (fluid + boundary kernels)
+    int fluid_blocks = 0;   // blocks of the fluid kernel
     int64_t device_bytes = 0;
     // parameters and state
     lbm_params params{};
@@ -98,23 +105,31 @@ void dev_free(lbm_ctx *c, void *p, size_t bytes) {
 }
 
 size_t pop_bytes(const lbm_ctx *c) { return (size_t)27 * (size_t)c->idx.nslots * storage_bytes(c->desc.precision); }
+size_t margin_bytes(const lbm_ctx *c) { return (size_t)buffer_margin(c->desc.nx) * storage_bytes(c->desc.precision); }
+size_t raw_pop_bytes(const lbm_ctx *c) { return pop_bytes(c) + 2 * margin_bytes(c); }
+size_t raw_mask_bytes(const lbm_ctx *c) { return ((size_t)c->idx.nslots + 2 * MASK_MARGIN) * 4; }
 
 void release_geometry(lbm_ctx *c) {
     const size_t ns = (size_t)c->idx.nslots;
-    dev_free(c, c->f[0], pop_bytes(c));
-    dev_free(c, c->f[1], pop_bytes(c));
-    dev_free(c, c->d_mask, ns * 4);
-    dev_free(c, c->d_row_base, c->idx.row_base.size() * 4);
+    dev_free(c, c->f_raw[0], raw_pop_bytes(c));
+    dev_free(c, c->f_raw[1], raw_pop_bytes(c));
+    dev_free(c, c->d_mask_raw, raw_mask_bytes(c));
+    dev_free(c, c->d_segs, c->idx.segs.size() * 16);
+    dev_free(c, c->d_row_nb, c->idx.row_nb.size() * 4);
     dev_free(c, c->d_chunks, c->idx.chunks.size() * 8);
+    dev_free(c, c->d_bnodes, c->idx.bnodes.size() * 16);
     dev_free(c, c->d_slot_of_active, c->idx.slot_of_active.size() * 4);
     dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     dev_free(c, c->d_health, 8 * 8);
     dev_free(c, c->d_status, 256);
     dev_free(c, c->d_stats, 2 * ns * 8);
     c->f[0] = c->f[1] = nullptr;
-    c->d_mask = nullptr;
-    c->d_row_base = nullptr;
+    c->f_raw[0] = c->f_raw[1] = nullptr;
+    c->d_mask = c->d_mask_raw = nullptr;
+    c->d_segs = nullptr;
+    c->d_row_nb = nullptr;
     c->d_chunks = nullptr;
+    c->d_bnodes = nullptr;
     c->d_slot_of_active = nullptr;
     c->d_partials = nullptr;
     c->d_health = nullptr;
@@ -149,7 +164,15 @@ lbm_status need(lbm_ctx *c, bool geom, bool params, bool state) {
     return LBM_OK;
 }
 
+// Ghost slots and periodic copies of the current buffer from its active cells.
+cudaError_t fill_ghosts(lbm_ctx *c) {
+    return DISPATCH(c->desc.precision, launch_fill_ghosts, c->f[c->cur], c->d_mask, c->d_chunks, c->d_row_nb,
+                    (int32_t)c->idx.chunks.size(), c->d_bnodes, (int32_t)c->idx.bnodes.size(), c->idx.nslots,
+                    c->desc.nx, (c->desc.periodic & LBM_PERIODIC_X) ? 1 : 0, c->stream);
+}
+
 lbm_status reset_state(lbm_ctx *c) {
+    CK(fill_ghosts(c), "fill ghost slots");
     c->t = 0;
     c->stats_samples = 0;
     c->stats_on = false;
@@ -234,35 +257,51 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     release_geometry(c);
     c->idx = std::move(idx);
     const size_t ns = (size_t)c->idx.nslots;
-    c->nblocks = reduce_blocks((int32_t)c->idx.chunks.size());
-    c->f[0] = dev_alloc(c, pop_bytes(c));
-    c->f[1] = dev_alloc(c, pop_bytes(c));
-    c->d_mask = (uint32_t *)dev_alloc(c, ns * 4);
-    c->d_row_base = (int32_t *)dev_alloc(c, c->idx.row_base.size() * 4);
+    c->fluid_blocks = DISPATCH(c->desc.precision, step_fluid_blocks, (int32_t)c->idx.chunks.size(),
+                               (int32_t)(c->idx.segs.size() / SEG_RECORD_INT4), c->desc.device);
+    c->step_blocks = c->fluid_blocks + node_blocks((int64_t)c->idx.bnodes.size());
+    c->nblocks = std::max(c->step_blocks, node_blocks(c->idx.n_active));
+    for (int k = 0; k < 2; ++k) {
+        c->f_raw[k] = dev_alloc(c, raw_pop_bytes(c));
+        c->f[k] = c->f_raw[k] ? static_cast<char *>(c->f_raw[k]) + margin_bytes(c) : nullptr;
+    }
+    c->d_mask_raw = (uint32_t *)dev_alloc(c, raw_mask_bytes(c));
+    c->d_mask = c->d_mask_raw ? c->d_mask_raw + MASK_MARGIN : nullptr;
+    c->d_segs = (int4 *)dev_alloc(c, c->idx.segs.size() * 16);
+    c->d_row_nb = (int4 *)dev_alloc(c, c->idx.row_nb.size() * 4);
     c->d_chunks = (int2 *)dev_alloc(c, c->idx.chunks.size() * 8);
+    c->d_bnodes = (int4 *)dev_alloc(c, c->idx.bnodes.size() * 16);
     c->d_slot_of_active = (int32_t *)dev_alloc(c, c->idx.slot_of_active.size() * 4);
     c->d_partials = (double *)dev_alloc(c, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     c->d_health = (double *)dev_alloc(c, 8 * 8);
     c->d_status = (uint32_t *)dev_alloc(c, 256);
-    if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_base || !c->d_chunks || !c->d_slot_of_active ||
+    if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_nb || !c->d_chunks || !c->d_bnodes || !c->d_segs || !c->d_slot_of_active ||
         !c->d_partials || !c->d_health || !c->d_status) {
         release_geometry(c);
         return fail(c, LBM_ERR_OOM, "device allocation failed in lbm_set_geometry");
     }
+    CK(cudaMemsetAsync(c->d_mask_raw, 0, raw_mask_bytes(c), c->stream), "clear link words");
     CK(cudaMemcpyAsync(c->d_mask, c->idx.mask.data(), ns * 4, cudaMemcpyHostToDevice, c->stream), "copy mask");
-    CK(cudaMemcpyAsync(c->d_row_base, c->idx.row_base.data(), c->idx.row_base.size() * 4, cudaMemcpyHostToDevice,
+    if (!c->idx.segs.empty())
+        CK(cudaMemcpyAsync(c->d_segs, c->idx.segs.data(), c->idx.segs.size() * 16, cudaMemcpyHostToDevice, c->stream),
+           "copy segments");
+    CK(cudaMemcpyAsync(c->d_row_nb, c->idx.row_nb.data(), c->idx.row_nb.size() * 4, cudaMemcpyHostToDevice,
                        c->stream),
-       "copy row_base");
+       "copy row records");
     CK(cudaMemcpyAsync(c->d_chunks, c->idx.chunks.data(), c->idx.chunks.size() * 8, cudaMemcpyHostToDevice,
                        c->stream),
        "copy chunks");
+    if (!c->idx.bnodes.empty())
+        CK(cudaMemcpyAsync(c->d_bnodes, c->idx.bnodes.data(), c->idx.bnodes.size() * 16, cudaMemcpyHostToDevice,
+                           c->stream),
+           "copy boundary nodes");
     CK(cudaMemcpyAsync(c->d_slot_of_active, c->idx.slot_of_active.data(), c->idx.slot_of_active.size() * 4,
                        cudaMemcpyHostToDevice, c->stream),
        "copy slot map");
     // Padding slots are never read by the step kernel; zero both buffers so
     // that checkpoints and dumps are deterministic.
-    CK(cudaMemsetAsync(c->f[0], 0, pop_bytes(c), c->stream), "clear f0");
-    CK(cudaMemsetAsync(c->f[1], 0, pop_bytes(c), c->stream), "clear f1");
+    CK(cudaMemsetAsync(c->f_raw[0], 0, raw_pop_bytes(c), c->stream), "clear f0");
+    CK(cudaMemsetAsync(c->f_raw[1], 0, raw_pop_bytes(c), c->stream), "clear f1");
     CK(cudaMemsetAsync(c->d_status, 0, 4, c->stream), "clear status");
     CK(cudaStreamSynchronize(c->stream), "sync geometry upload");
     c->has_geom = true;
@@ -425,25 +464,39 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
     DeviceGuard g(c->desc.device);
     StepArgs a{};
     a.mask = c->d_mask;
-    a.row_base = c->d_row_base;
+    a.row_nb = c->d_row_nb;
     a.chunks = c->d_chunks;
     a.stride = c->idx.nslots;
     a.nchunks = (int32_t)c->idx.chunks.size();
+    a.bnodes = c->d_bnodes;
+    a.nbnodes = (int32_t)c->idx.bnodes.size();
+    a.fluid_blocks = c->fluid_blocks;
+    a.segs = c->d_segs;
+    a.nsegs = (int32_t)(c->idx.segs.size() / SEG_RECORD_INT4);
+    a.status = c->d_status;
     a.nx = c->desc.nx;
     a.ny = c->desc.ny;
     a.nz = c->desc.nz;
+    a.ny_e = c->idx.ny_e;
+    a.periodic_x = (c->desc.periodic & LBM_PERIODIC_X) ? 1 : 0;
     a.profile = c->params.inlet_profile;
-    a.omega = c->omega;
-    a.ghost[0] = c->params.omega3;
-    a.ghost[1] = c->params.omega4;
-    a.ghost[2] = c->params.omega5;
-    a.ghost[3] = c->params.omega6;
-    a.u_in = c->params.u_in;
-    a.d_in = c->params.d_in;
-    a.axis_x = c->params.axis_x;
-    a.axis_y = c->params.axis_y;
-    a.noise_amp = c->params.noise_amp;
-    a.rho_out = c->params.rho_out;
+    const double gr[4] = {c->params.omega3, c->params.omega4, c->params.omega5, c->params.omega6};
+    a.pd.omega = c->omega;
+    for (int q = 0; q < 4; ++q) a.pd.ghost[q] = gr[q];
+    a.pd.u_in = c->params.u_in;
+    a.pd.d_in = c->params.d_in;
+    a.pd.axis_x = c->params.axis_x;
+    a.pd.axis_y = c->params.axis_y;
+    a.pd.noise_amp = c->params.noise_amp;
+    a.pd.rho_out = c->params.rho_out;
+    a.pf.omega = (float)a.pd.omega;
+    for (int q = 0; q < 4; ++q) a.pf.ghost[q] = (float)gr[q];
+    a.pf.u_in = (float)a.pd.u_in;
+    a.pf.d_in = (float)a.pd.d_in;
+    a.pf.axis_x = (float)a.pd.axis_x;
+    a.pf.axis_y = (float)a.pd.axis_y;
+    a.pf.noise_amp = (float)a.pd.noise_amp;
+    a.pf.rho_out = (float)a.pd.rho_out;
     a.seed = c->params.noise_seed;
     a.scale = fp16_scale(c);
     a.inv_scale = 1.0f / a.scale;
@@ -462,7 +515,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
             ++c->stats_samples;
         }
         CK(DISPATCH(c->desc.precision, launch_step, a, c->ghost1, c->stream), "step kernel");
-        if (check) CK(launch_finalize(c->d_partials, c->nblocks, c->d_health, c->d_status, c->stream), "finalize");
+        if (check) CK(launch_finalize(c->d_partials, c->step_blocks, c->d_health, c->d_status, c->stream), "finalize");
         c->cur = 1 - c->cur;
         c->t = t_new;
     }
@@ -481,6 +534,7 @@ lbm_status lbm_sync(lbm_ctx *c) {
         CK(cudaMemcpyAsync(c->health, c->d_health, 6 * 8, cudaMemcpyDeviceToHost, c->stream), "read health");
         CK(cudaStreamSynchronize(c->stream), "sync health");
     }
+    if (status & 2u) return fail(c, LBM_ERR_TIMEOUT, "a bounded device-side wait gave up (step kernel)");
     if (status & 1u) return fail(c, LBM_ERR_UNSTABLE, "a health check found non-finite populations");
     return LBM_OK;
 }
@@ -530,10 +584,10 @@ lbm_status lbm_get_totals(lbm_ctx *c, double *mass, double mom[3]) {
     lbm_status st = need(c, true, false, true);
     if (st) return st;
     DeviceGuard g(c->desc.device);
-    CK(DISPATCH(c->desc.precision, launch_reduce, c->f[c->cur], c->d_mask, c->d_chunks, c->d_row_base,
-                (int32_t)c->idx.chunks.size(), c->idx.nslots, 1.0f / fp16_scale(c), c->d_partials, c->stream),
+    CK(DISPATCH(c->desc.precision, launch_reduce, c->f[c->cur], c->d_slot_of_active, c->idx.n_active, c->idx.nslots,
+                1.0f / fp16_scale(c), c->d_partials, c->stream),
        "reduce");
-    CK(launch_finalize(c->d_partials, c->nblocks, c->d_health, c->d_status, c->stream), "finalize");
+    CK(launch_finalize(c->d_partials, node_blocks(c->idx.n_active), c->d_health, c->d_status, c->stream), "finalize");
     CK(cudaMemcpyAsync(c->health, c->d_health, 6 * 8, cudaMemcpyDeviceToHost, c->stream), "read totals");
     CK(cudaStreamSynchronize(c->stream), "sync totals");
     if (mass) *mass = c->health[0];

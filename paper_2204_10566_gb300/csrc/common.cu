@@ -4,10 +4,12 @@
 
 namespace lbm {
 
-int reduce_blocks(int32_t nchunks) {
+int fluid_blocks(int32_t nchunks) {
     const int64_t threads = (int64_t)nchunks * CHUNK;
     return (int)((threads + STEP_THREADS - 1) / STEP_THREADS);
 }
+
+int node_blocks(int64_t n) { return (int)((n + STEP_THREADS - 1) / STEP_THREADS); }
 
 // One block sums the per-block partials in a fixed order (each thread a
 // fixed strided subset, then a fixed tree), so the totals are bitwise

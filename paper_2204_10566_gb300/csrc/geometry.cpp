@@ -1,12 +1,19 @@
 // Host-side geometry: nozzle voxeliser and the fluid-only sparse index.
 //
-// Storage layout ("slots"): the active cells of each row (fixed y, z) are
-// stored x-contiguously; a row occupies [xb, xe) rounded outward to CHUNK
-// boundaries, so slot = row_base[row] + x with row_base a multiple of CHUNK.
-// Cells inside a row's span that are solid become padding slots (never
-// updated, never pulled from).  Each slot carries a 32-bit link word: one
-// bounce-back bit per population, the node type and, for inlet/outlet nodes,
-// the direction of the interior partner used by the extrapolation.
+// Storage layout ("slots"): rows are the x-lines of the box extended by one
+// layer in y and z (row = (y+1) + (ny+2)(z+1)).  A row stores, x-contiguously,
+// every position that the step kernel reads or writes in it: its active
+// cells, the ghost positions of wall links (a solid or outside position
+// x - c_i next to an active fluid cell x) and, for a periodic x axis, the two
+// wrap-around copies at x = -1 and x = nx.  Each row's stored range is
+// rounded outward to CHUNK boundaries, so slot = base(row) + x with base a
+// multiple of CHUNK.  Solid cells inside a stored range are padding.
+//
+// Because every pull source x - c_i has a slot (an active cell, a ghost slot
+// holding the reflected population, or a periodic copy), the kernel's gather
+// is branch-free: slot = nb[j] + x - cx, with nb the row's neighbour bases.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,42 +36,99 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                      (long long)b);
             return msg;
         }
-    const int64_t nrows = (int64_t)ny * nz;
-    if (nrows > INT32_MAX) return "too many rows";
+    if (nx > (int)CHUNK_X0_MASK) return "nx too large (at most 2^20 - 1)";
     out = HostIndex();
-    out.row_base.assign((size_t)nrows, 0);
-    std::vector<int> xb((size_t)nrows, -1), xe((size_t)nrows, -1);
-    for (int64_t r = 0; r < nrows; ++r) {
-        const uint8_t *row = flags + r * nx;
-        for (int x = 0; x < nx; ++x)
-            if (row[x] != LBM_SOLID) {
-                if (xb[r] < 0) xb[r] = x;
-                xe[r] = x + 1;
+    const bool px = periodic & LBM_PERIODIC_X, py = periodic & LBM_PERIODIC_Y, pz = periodic & LBM_PERIODIC_Z;
+    const int ny_e = ny + 2, nz_e = nz + 2;
+    const int64_t nrows = (int64_t)ny_e * nz_e;
+    if (nrows > INT32_MAX / 4) return "too many rows";
+    out.ny_e = ny_e;
+    out.nz_e = nz_e;
+    auto row_of = [&](int y, int z) -> int64_t { return (int64_t)(y + 1) + (int64_t)ny_e * (z + 1); };
+    // resolve a pull source (x, y, z) (each coordinate at most one step outside
+    // the box): returns its flag (SOLID when outside a non-periodic face) and
+    // the coordinates used for storage (y, z wrapped when periodic; x wrapped
+    // only for the flag lookup).
+    auto source = [&](int x, int y, int z, int &ys, int &zs) -> int {
+        bool outside = false;
+        int xw = x, yw = y, zw = z;
+        if (x < 0 || x >= nx) { if (px) xw = (x + nx) % nx; else outside = true; }
+        if (y < 0 || y >= ny) { if (py) yw = (y + ny) % ny; else outside = true; }
+        if (z < 0 || z >= nz) { if (pz) zw = (z + nz) % nz; else outside = true; }
+        ys = py ? yw : y;
+        zs = pz ? zw : z;
+        if (outside) return LBM_SOLID;
+        return flags[box_index(xw, yw, zw, nx, ny)];
+    };
+
+    std::vector<int> need_lo((size_t)nrows, INT_MAX), need_hi((size_t)nrows, INT_MIN);
+    std::vector<int> act_lo((size_t)nrows, INT_MAX), act_hi((size_t)nrows, INT_MIN);  // fluid cells
+    auto need = [&](int64_t r, int x) {
+        if (x < need_lo[r]) need_lo[r] = x;
+        if (x > need_hi[r]) need_hi[r] = x;
+    };
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int fl = flags[box_index(x, y, z, nx, ny)];
+                if (fl == LBM_SOLID) continue;
+                const int64_t r = row_of(y, z);
+                need(r, x);
+                if (fl == LBM_FLUID) {
+                    if (x < act_lo[r]) act_lo[r] = x;
+                    if (x > act_hi[r]) act_hi[r] = x;
+                }
+                if (px && x == nx - 1) need(r, -1);
+                if (px && x == 0) need(r, nx);
+                if (fl != LBM_FLUID) continue;
+                for (int i = 0; i < 27; ++i) {
+                    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+                    int ys, zs;
+                    if (source(x - cx, y - cy, z - cz, ys, zs) == LBM_SOLID) need(row_of(ys, zs), x - cx);
+                }
             }
-    }
+    std::vector<int32_t> base((size_t)nrows, 0);
     int64_t next = 0;
     for (int64_t r = 0; r < nrows; ++r) {
-        if (xb[r] < 0) continue;
-        const int lo = xb[r] & ~(CHUNK - 1);
-        const int hi = (xe[r] + CHUNK - 1) & ~(CHUNK - 1);
-        out.row_base[r] = (int32_t)(next - lo);
-        for (int x0 = lo; x0 < xe[r]; x0 += CHUNK) out.chunks.push_back(make_int2((int)r, x0));
+        if (need_lo[r] == INT_MAX) continue;
+        const int lo = (int)std::floor(need_lo[r] / (double)CHUNK) * CHUNK;
+        const int hi = ((need_hi[r] + 1 + CHUNK - 1) / CHUNK) * CHUNK;
+        base[r] = (int32_t)(next - lo);
         next += hi - lo;
-        if (next > (int64_t)INT32_MAX - 64) return "lattice too large for 32-bit slot indices";
+        if (next > (int64_t)INT32_MAX / 2) return "lattice too large for 32-bit slot indices";
     }
     out.nslots = (next + 63) & ~(int64_t)63;
-    if (out.nslots == 0) return "geometry has no active cells";
-    if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
     out.mask.assign((size_t)out.nslots, (uint32_t)TYPE_PAD << TYPE_SHIFT);
+    out.row_nb.assign((size_t)nrows * ROW_RECORD_INTS, 0);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y) {
+            const int64_t r = row_of(y, z);
+            if (need_lo[r] == INT_MAX) continue;
+            for (int j = 0; j < 9; ++j) {
+                const int cy = j % 3 - 1, cz = j / 3 - 1;
+                int yy = y - cy, zz = z - cz;
+                if (py) yy = (yy + ny) % ny;
+                if (pz) zz = (zz + nz) % nz;
+                out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(yy, zz)];
+            }
+            if (act_lo[r] == INT_MAX) continue;
+            const int32_t *nbr = &out.row_nb[(size_t)r * ROW_RECORD_INTS];
+            for (int x0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; x0 <= act_hi[r]; x0 += SEGMENT) {
+                out.segs.push_back(make_int4((int)r, x0, std::min(SEGMENT, act_hi[r] + 1 - x0), nbr[8]));
+                out.segs.push_back(make_int4(nbr[0], nbr[1], nbr[2], nbr[3]));
+                out.segs.push_back(make_int4(nbr[4], nbr[5], nbr[6], nbr[7]));
+            }
+            for (int x0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; x0 <= act_hi[r]; x0 += CHUNK) {
+                uint32_t lanes = 0;
+                for (int l = 0; l < CHUNK; ++l) {
+                    const int x = x0 + l;
+                    if (x < nx && flags[box_index(x, y, z, nx, ny)] == LBM_FLUID) lanes |= 1u << l;
+                }
+                out.chunks.push_back(make_int2((int)r, (int)((uint32_t)x0 | (lanes << CHUNK_LANES_SHIFT))));
+            }
+        }
+    if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
 
-    const bool px = periodic & LBM_PERIODIC_X, py = periodic & LBM_PERIODIC_Y, pz = periodic & LBM_PERIODIC_Z;
-    auto flag_at = [&](int x, int y, int z, bool &inside) -> int {
-        inside = true;
-        if (x < 0 || x >= nx) { if (!px) { inside = false; return LBM_SOLID; } x = (x + nx) % nx; }
-        if (y < 0 || y >= ny) { if (!py) { inside = false; return LBM_SOLID; } y = (y + ny) % ny; }
-        if (z < 0 || z >= nz) { if (!pz) { inside = false; return LBM_SOLID; } z = (z + nz) % nz; }
-        return flags[box_index(x, y, z, nx, ny)];
-    };
     static const int dirs[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -72,21 +136,23 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                 const int64_t b = box_index(x, y, z, nx, ny);
                 const int fl = flags[b];
                 if (fl == LBM_SOLID) continue;
-                const int64_t r = (int64_t)y + (int64_t)ny * z;
-                const int32_t slot = out.row_base[r] + x;
-                uint32_t m = 0;
-                for (int i = 0; i < 27; ++i) {
-                    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-                    bool inside;
-                    if (flag_at(x - cx, y - cy, z - cz, inside) == LBM_SOLID) m |= 1u << i;
-                }
-                uint32_t type = TYPE_FLUID, dir = 0;
-                if (fl == LBM_INLET || fl == LBM_OUTLET) {
+                const int32_t slot = base[row_of(y, z)] + x;
+                uint32_t m = 0, type = TYPE_FLUID, dir = 0;
+                if (fl == LBM_FLUID) {
+                    for (int i = 0; i < 27; ++i) {
+                        const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+                        int ys, zs;
+                        if (source(x - cx, y - cy, z - cz, ys, zs) == LBM_SOLID) {
+                            m |= 1u << i;
+                            ++out.n_ghost;
+                        }
+                    }
+                } else {
                     type = fl == LBM_INLET ? TYPE_INLET : TYPE_OUTLET;
                     int count = 0;
                     for (int k = 0; k < 6; ++k) {
-                        bool inside;
-                        if (flag_at(x + dirs[k][0], y + dirs[k][1], z + dirs[k][2], inside) == LBM_FLUID) {
+                        int ys, zs;
+                        if (source(x + dirs[k][0], y + dirs[k][1], z + dirs[k][2], ys, zs) == LBM_FLUID) {
                             ++count;
                             dir = (uint32_t)k;
                         }
@@ -100,14 +166,109 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                     }
                 }
                 out.mask[(size_t)slot] = m | (type << TYPE_SHIFT) | (dir << DIR_SHIFT);
+                if (type != TYPE_FLUID)
+                    out.bnodes.push_back(make_int4(x, (int)row_of(y, z), slot, (int)out.mask[(size_t)slot]));
                 out.slot_of_active.push_back(slot);
                 out.box_of_active.push_back(b);
             }
     out.n_active = (int64_t)out.slot_of_active.size();
+    if (out.n_active == 0) return "geometry has no active cells";
+    return "";
+}
+
+// Structural invariants of an index, re-derived independently of how
+// build_index produced it: segment and chunk records, alignment and bounds of
+// every staged copy, and the pull slot of every link of every fluid cell.
+std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, int ny, int nz, int periodic) {
+    const int64_t ns = ix.nslots;
+    const int64_t nrows = (int64_t)ix.ny_e * ix.nz_e;
+    if (ix.segs.size() % SEG_RECORD_INT4) return "segment records are not whole";
+    if (ix.row_nb.size() != (size_t)nrows * ROW_RECORD_INTS) return "row record count";
+    const int64_t margin = buffer_margin(nx);
+    std::vector<uint8_t> seen((size_t)nx * ny * nz, 0);
+    for (size_t k = 0; k < ix.segs.size(); k += SEG_RECORD_INT4) {
+        const int4 h = ix.segs[k], a = ix.segs[k + 1], b = ix.segs[k + 2];
+        const int nb[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, h.w};
+        const int r = h.x, x0 = h.y, count = h.z;
+        if (r < 0 || r >= nrows || x0 < 0 || x0 % CHUNK || count < 1 || count > SEGMENT || x0 + count > nx)
+            return "bad segment header";
+        const int y = r % ix.ny_e - 1, z = r / ix.ny_e - 1;
+        if (y < 0 || y >= ny || z < 0 || z >= nz) return "segment row outside the box";
+        for (int j = 0; j < 9; ++j)
+            if (nb[j] != ix.row_nb[(size_t)r * ROW_RECORD_INTS + j] || nb[j] % CHUNK) return "segment row bases";
+        for (int S = 2; S <= 8; S *= 2) {  // FP16, FP32, FP64 element sizes
+            const int halo = 16 / S;
+            const int64_t n_el = ((count + 2 * halo + halo - 1) / halo) * halo;
+            for (int i = 0; i < 27; ++i) {
+                const int64_t start = (int64_t)i * ns + nb[i / 3] + x0 - halo;
+                if ((start * S) % 16) return "staged copy not 16-byte aligned";
+                if (start < -margin || start + n_el > 27 * ns + margin) return "staged copy leaves the buffer";
+            }
+        }
+        const int64_t mstart = (int64_t)nb[4] + x0 - 4, n_mask = ((count + 8 + 3) / 4) * 4;
+        if (mstart % 4 || mstart < -MASK_MARGIN || mstart + n_mask > ns + MASK_MARGIN) return "link-word copy bounds";
+        for (int x = x0; x < x0 + count; ++x) {
+            const int64_t bx = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
+            if (flags[bx] == LBM_FLUID) {
+                if (seen[bx]++) return "fluid cell in two segments";
+            }
+        }
+    }
+    for (int64_t b = 0; b < (int64_t)seen.size(); ++b)
+        if ((flags[b] == LBM_FLUID) != (seen[b] == 1)) return "fluid cell not covered by exactly one segment";
+    std::fill(seen.begin(), seen.end(), 0);
+    for (const int2 &c : ix.chunks) {
+        const int r = c.x, x0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
+        const uint32_t lanes = ((uint32_t)c.y >> CHUNK_LANES_SHIFT) & 0xFFu;
+        if (r < 0 || r >= nrows || x0 % CHUNK) return "bad chunk";
+        const int y = r % ix.ny_e - 1, z = r / ix.ny_e - 1;
+        for (int l = 0; l < CHUNK; ++l) {
+            if (!((lanes >> l) & 1u)) continue;
+            const int x = x0 + l;
+            if (x >= nx) return "chunk lane outside the box";
+            const int64_t bx = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
+            if (flags[bx] != LBM_FLUID || seen[bx]++) return "chunk lane is not a unique fluid cell";
+        }
+    }
+    // pulls of every fluid cell land on stored slots
+    for (int64_t k = 0; k < ix.n_active; ++k) {
+        const int64_t bx = ix.box_of_active[k];
+        if (flags[bx] != LBM_FLUID) continue;
+        const int x = (int)(bx % nx), y = (int)((bx / nx) % ny), z = (int)(bx / ((int64_t)nx * ny));
+        const int32_t *nb = &ix.row_nb[(size_t)((y + 1) + (int64_t)ix.ny_e * (z + 1)) * ROW_RECORD_INTS];
+        if (nb[4] + x != ix.slot_of_active[k]) return "slot of an active cell";
+        for (int i = 0; i < 27; ++i) {
+            const int64_t s = (int64_t)nb[i / 3] + x - (i % 3 - 1);
+            if (s < 0 || s >= ns) return "pull slot outside the buffer";
+        }
+    }
+    for (const int4 &n : ix.bnodes)
+        if (n.z < 0 || n.z >= ns || ix.row_nb[(size_t)n.y * ROW_RECORD_INTS + 4] + n.x != n.z) return "boundary node";
+    (void)periodic;
     return "";
 }
 
 }  // namespace lbm
+
+// Host-only check of a flag field and its sparse index (C ABI, lbm.h).
+extern "C" lbm_status lbm_check_layout(const uint8_t *flags, int32_t nx, int32_t ny, int32_t nz, int32_t periodic,
+                                       int64_t out[8]) {
+    if (!flags || nx < 1 || ny < 1 || nz < 1 || (periodic & ~7)) return LBM_ERR_ARG;
+    lbm::HostIndex ix;
+    if (!lbm::build_index(flags, nx, ny, nz, periodic, ix).empty()) return LBM_ERR_ARG;
+    if (!lbm::validate_index(ix, flags, nx, ny, nz, periodic).empty()) return LBM_ERR_STATE;
+    if (out) {
+        out[0] = ix.n_active;
+        out[1] = ix.nslots;
+        out[2] = (int64_t)(ix.segs.size() / lbm::SEG_RECORD_INT4);
+        out[3] = (int64_t)ix.chunks.size();
+        out[4] = (int64_t)ix.bnodes.size();
+        out[5] = ix.n_ghost;
+        out[6] = (int64_t)ix.ny_e * ix.nz_e;
+        out[7] = 0;
+    }
+    return LBM_OK;
+}
 
 // Nozzle voxeliser (C ABI, declared in lbm.h).
 extern "C" lbm_status lbm_make_nozzle(int32_t D, int32_t d, int32_t L_in, int32_t L_cone, int32_t L_throat,

@@ -11,17 +11,29 @@
 //
 // GB300 design: one thread per active cell, pull scheme over a fluid-only
 // slot layout (rows of x-contiguous cells), structure-of-arrays populations
-// stored as deviations from the lattice weights.  Because T(u) is the tensor
-// product of three 1-D 3x3 transforms, T and its inverse are applied as a
-// cascade of 1-D passes in registers; with the default ghost rates only the
-// six second-order central moments survive relaxation and the inverse is the
+// stored as deviations from the lattice weights.  Every pull source has a
+// slot (wall links read a ghost slot the cell filled with its reflected
+// population in the previous step), so the gather is 27 unconditional
+// coalesced loads at nb[j] + x - cx.  Because T(u) is the tensor product of
+// three 1-D 3x3 transforms, T and its inverse are applied as a cascade of
+// 1-D passes in registers; with the default ghost rates only the six
+// second-order central moments survive relaxation and the inverse is the
 // product-form equilibrium plus six correction terms.
 #pragma once
 
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "lbm_internal.h"
+
+// Minimum resident blocks per SM requested for the step kernel (caps its
+// registers: 65536 / (256 * blocks)).
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 3
+#endif
 
 namespace lbm {
 
@@ -35,6 +47,7 @@ struct Storage<0> {  // FP64 deviations
     using T = double;
     using R = double;
     static __device__ __forceinline__ R load(const T *p, R) { return __ldg(p); }
+    static __device__ __forceinline__ R load_shared(const T *p, R) { return *p; }
     static __device__ __forceinline__ void store(T *p, R v, R) { *p = v; }
 };
 
@@ -43,6 +56,7 @@ struct Storage<1> {  // FP32 deviations
     using T = float;
     using R = float;
     static __device__ __forceinline__ R load(const T *p, R) { return __ldg(p); }
+    static __device__ __forceinline__ R load_shared(const T *p, R) { return *p; }
     static __device__ __forceinline__ void store(T *p, R v, R) { *p = v; }
 };
 
@@ -51,6 +65,7 @@ struct Storage<2> {  // FP16 (f - w) * s, FP32 arithmetic
     using T = __half;
     using R = float;
     static __device__ __forceinline__ R load(const T *p, R inv_s) { return __half2float(__ldg(p)) * inv_s; }
+    static __device__ __forceinline__ R load_shared(const T *p, R inv_s) { return __half2float(*p) * inv_s; }
     static __device__ __forceinline__ void store(T *p, R v, R s) { *p = __float2half_rn(v * s); }
 };
 
@@ -112,7 +127,34 @@ __device__ __forceinline__ void eq_deviation(R rho, const Axis<R> &X, const Axis
     }
 }
 
+// d_i += f^eq_i(rho_b, u_b) - f^eq_i(rho_f, u_f), line by line so that only
+// a few values are live besides d (keeps the boundary path from raising the
+// register count of the whole kernel).
+template <class R>
+__device__ __forceinline__ void add_eq_difference(R rb, R uxb, R uyb, R uzb, R rf, R uxf, R uyf, R uzf,
+                                                  R (&d)[27]) {
+    const Axis<R> Xb(uxb), Yb(uyb), Zb(uzb), Xf(uxf), Yf(uyf), Zf(uzf);
+    const R db = rb - R(1), df = rf - R(1);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const int cy = j % 3 - 1, cz = j / 3 - 1;
+        const R wy = w1<R>(cy), wz = w1<R>(cz);
+        const R Eb = Yb.g0[cy + 1] * Zb.g0[cz + 1], Ef = Yf.g0[cy + 1] * Zf.g0[cz + 1];
+        const R Db = Yb.d[cy + 1] * Zb.g0[cz + 1] + wy * Zb.d[cz + 1];
+        const R Df = Yf.d[cy + 1] * Zf.g0[cz + 1] + wy * Zf.d[cz + 1];
+#pragma unroll
+        for (int cx = -1; cx <= 1; ++cx) {
+            const R w = w1<R>(cx) * wy * wz;
+            d[3 * j + cx + 1] += (db * w + rb * (Xb.d[cx + 1] * Eb + w1<R>(cx) * Db)) -
+                                 (df * w + rf * (Xf.d[cx + 1] * Ef + w1<R>(cx) * Df));
+        }
+    }
+}
+
 // --------------------------------------------------------------- collision
+
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Collision with the default ghost rates (all 1).  d holds f_i - w_i on entry
 // and f*_i - w_i on exit; rho, u receive the (conserved) moments.
@@ -147,7 +189,7 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
         if (cy != 0 && cz != 0) pyz += (cy * cz) > 0 ? s0[j] : -s0[j];
     }
     rho = R(1) + drho;
-    const R inv = R(1) / rho;
+    const R inv = recip(rho);
     ux = jx * inv;
     uy = jy * inv;
     uz = jz * inv;
@@ -163,23 +205,31 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
     const R Ayz = k * (pyz - rho * uy * uz);
     // Inverse: f* = rho prod g0 + sum over the six relaxed second-order moments
     // of A_m prod_a g_{m_a}; orders 1 and 3..6 are zero after relaxation.
-    const Axis<R> X(ux), Y(uy), Z(uz);
+    // Per (cy, cz) line the x-dependence is spanned by {w, d, g1, g2}(cx):
+    //   f*_i - w_i = wx Bw + dx Bd + g1x B1 + g2x B2,
+    // and for cx = +-1 this splits into S +- A.
+    const Axis<R> Y(uy), Z(uz);
+    const R h = R(0.5);
+    const R ux2h = h * ux * ux, uxh = h * ux;
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
         const int cy = j % 3 - 1, cz = j / 3 - 1;
-        const R wy = w1<R>(cy), wz = w1<R>(cz);
+        const R wy = w1<R>(cy);
         const R gy0 = Y.g0[cy + 1], gz0 = Z.g0[cz + 1], gy1 = Y.g1[cy + 1], gz1 = Z.g1[cz + 1];
         const R E = gy0 * gz0;
         const R D = Y.d[cy + 1] * gz0 + wy * Z.d[cz + 1];
         const R C0 = Ayy * g2<R>(cy) * gz0 + Azz * gy0 * g2<R>(cz) + Ayz * gy1 * gz1;
-        const R C1 = Axy * gy1 * gz0 + Axz * gy0 * gz1;
-        const R C2 = Axx * E;
-#pragma unroll
-        for (int cx = -1; cx <= 1; ++cx) {
-            const R wx = w1<R>(cx);
-            d[3 * j + cx + 1] = drho * (wx * wy * wz) + rho * (X.d[cx + 1] * E + wx * D) +
-                                X.g0[cx + 1] * C0 + X.g1[cx + 1] * C1 + g2<R>(cx) * C2;
-        }
+        const R B1 = Axy * gy1 * gz0 + Axz * gy0 * gz1;
+        const R B2 = Axx * E;
+        const R Bw = drho * (wy * w1<R>(cz)) + rho * D + C0;
+        const R Bd = rho * E + C0;
+        // cx = 0: w = 2/3, d = -ux^2, g1 = -2 ux, g2 = -1
+        d[3 * j + 1] = R(2) / R(3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
+        // cx = +-1: w = 1/6, d = (ux^2 +- ux)/2, g1 = ux +- 1/2, g2 = 1/2
+        const R S = R(1) / R(6) * Bw + ux2h * Bd + ux * B1 + h * B2;
+        const R A = uxh * Bd + h * B1;
+        d[3 * j + 2] = S + A;
+        d[3 * j] = S - A;
     }
 }
 
@@ -207,7 +257,7 @@ __device__ __forceinline__ void collide_general(R (&d)[27], R omega, const R (&g
         if (cz_of(i)) jz += cz_of(i) > 0 ? d[i] : -d[i];
     }
     rho = R(1) + drho;
-    const R inv = R(1) / rho;
+    const R inv = recip(rho);
     ux = jx * inv;
     uy = jy * inv;
     uz = jz * inv;
@@ -283,32 +333,38 @@ __device__ __forceinline__ void collide_general(R (&d)[27], R omega, const R (&g
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Pull gather of cell (x, y, z) at storage slot `slot` with link word m:
-// d_i = f*_i(x - c_i), or the halfway bounce-back f*_{26-i}(x) (Bouzidi's
-// interpolated bounce-back at q = 1/2, Sec. 2.2) when bit i of m is set.
-template <int P>
-__device__ __forceinline__ void gather(const StepArgs &a, int x, int y, int z, int slot, uint32_t m,
-                                       typename Storage<P>::R (&d)[27]) {
+// The nine neighbour-row bases of a row record (j = (cy+1) + 3 (cz+1)).
+__device__ __forceinline__ void load_row(const int4 *row_nb, int row, int (&nb)[9]) {
+    const int4 a = __ldg(row_nb + 3 * row), b = __ldg(row_nb + 3 * row + 1), c = __ldg(row_nb + 3 * row + 2);
+    nb[0] = a.x; nb[1] = a.y; nb[2] = a.z; nb[3] = a.w;
+    nb[4] = b.x; nb[5] = b.y; nb[6] = b.z; nb[7] = b.w;
+    nb[8] = c.x;
+}
+
+// Element offset of (population i, slot s): i * stride + s, in 32-bit
+// unsigned arithmetic when the buffer allows (see MAX_SLOTS_32).
+template <bool WIDE>
+__device__ __forceinline__ typename std::conditional<WIDE, int64_t, uint32_t>::type
+elem(int i, int64_t stride, int s) {
+    if constexpr (WIDE)
+        return (int64_t)i * stride + s;
+    else
+        return (uint32_t)i * (uint32_t)stride + (uint32_t)s;
+}
+
+// Pull gather of the cell at x in the row with bases nb: d_i = f*_i(x - c_i)
+// from slot nb[j] + x - cx of population array i.  For a wall link that slot
+// is the ghost slot holding f*_{26-i}(x) (halfway bounce-back, i.e.
+// Bouzidi's interpolated bounce-back at q = 1/2, Sec. 2.2).
+template <int P, bool WIDE>
+__device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], int x, typename Storage<P>::R (&d)[27]) {
     using S = Storage<P>;
     using T = typename S::T;
     using R = typename S::R;
     const T *fin = static_cast<const T *>(a.fin);
     const R inv_s = R(a.inv_scale);
-    int rb[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        const int ys = wrap(y - (j % 3 - 1), a.ny), zs = wrap(z - (j / 3 - 1), a.nz);
-        rb[j] = __ldg(a.row_base + zs * a.ny + ys);
-    }
-    const int xs[3] = {wrap(x + 1, a.nx), x, wrap(x - 1, a.nx)};
-#pragma unroll
-    for (int i = 0; i < 27; ++i) {
-        const int j = i / 3;
-        const bool bb = (m >> i) & 1u;
-        const int64_t off = bb ? (int64_t)(26 - i) * a.stride + slot
-                               : (int64_t)i * a.stride + (rb[j] + xs[i % 3]);
-        d[i] = S::load(fin + off, inv_s);
-    }
+    for (int i = 0; i < 27; ++i) d[i] = S::load(fin + elem<WIDE>(i, a.stride, nb[i / 3] + x - cx_of(i)), inv_s);
 }
 
 // ------------------------------------------------------------------- inlet
@@ -334,7 +390,7 @@ __device__ __forceinline__ R inlet_noise(uint64_t seed, int64_t step, int64_t no
 // -------------------------------------------------------- block reduction
 
 __device__ __forceinline__ void block_reduce_write(double (&v)[6], double *partials) {
-    __shared__ double sh[STEP_THREADS / 32][6];
+    __shared__ double sh[32][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -373,97 +429,369 @@ __device__ __forceinline__ void health_values(double rho, double ux, double uy, 
 
 // --------------------------------------------------------------- step kernel
 
-// One time step over all active cells (Sec. 2.1 evolution equation, pull
-// form).  Fluid cells gather + collide.  Inlet/outlet cells apply the
-// non-equilibrium extrapolation of Sec. 2.2 with their interior partner x_f,
-// whose update they recompute in place (same step, no second kernel):
-//   f*_i(x_b) = f^eq_i(rho_b, u_b) + f*_i(x_f) - f^eq_i(rho_f, u_f),
-// inlet: rho_b = rho_f, u_b prescribed; outlet: rho_b = rho_out, u_b = u_f.
+template <class R>
+__device__ __forceinline__ const FlowParams<R> &flow(const StepArgs &a);
+template <>
+__device__ __forceinline__ const FlowParams<double> &flow<double>(const StepArgs &a) { return a.pd; }
+template <>
+__device__ __forceinline__ const FlowParams<float> &flow<float>(const StepArgs &a) { return a.pf; }
+
 template <int P, bool GHOST1>
-__global__ void __launch_bounds__(STEP_THREADS) k_step(const StepArgs a) {
+__device__ __forceinline__ void collide(typename Storage<P>::R (&d)[27], const FlowParams<typename Storage<P>::R> &fp,
+                                        typename Storage<P>::R &rho, typename Storage<P>::R &ux,
+                                        typename Storage<P>::R &uy, typename Storage<P>::R &uz) {
+    if (GHOST1)
+        collide_ghost1(d, fp.omega, rho, ux, uy, uz);
+    else
+        collide_general(d, fp.omega, fp.ghost, rho, ux, uy, uz);
+}
+
+// Post-collision state of one cell is in d; write it to its own slot, the
+// ghost slots of its wall links, and (periodic x) its wrap-around copies.
+template <int P, bool WIDE>
+__device__ __forceinline__ void store_cell_state(const StepArgs &a, const int (&nb)[9], int x, int slot, uint32_t links,
+                                                 const typename Storage<P>::R (&d)[27]) {
     using S = Storage<P>;
     using T = typename S::T;
     using R = typename S::R;
+    const R s = R(a.scale);
+    T *fout = static_cast<T *>(a.fout);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) S::store(fout + elem<WIDE>(i, a.stride, slot), d[i], s);
+    if (links) {  // wall links: the reflected population waits in the ghost slot
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            if (!(links & (7u << (3 * j)))) continue;  // no wall link towards row j
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int i = 3 * j + c;
+                if (links & (1u << i)) S::store(fout + elem<WIDE>(i, a.stride, nb[j] + x - cx_of(i)), d[26 - i], s);
+            }
+        }
+    }
+    if (a.periodic_x) {  // wrap-around copies read across the periodic x faces
+        if (x == a.nx - 1) {
+#pragma unroll
+            for (int i = 2; i < 27; i += 3) S::store(fout + elem<WIDE>(i, a.stride, nb[4] - 1), d[i], s);
+        }
+        if (x == 0) {
+#pragma unroll
+            for (int i = 0; i < 27; i += 3) S::store(fout + elem<WIDE>(i, a.stride, nb[4] + a.nx), d[i], s);
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, R ux, R uy, R uz, double (&hv)[6]) {
+    if (a.flags & STEP_STATS) {
+        const double w = (double)uz;
+        a.stats[slot] += w;
+        a.stats[a.stride + slot] += w * w;
+    }
+    if (a.flags & STEP_REDUCE) health_values(rho, ux, uy, uz, hv);
+}
+
+// One time step of every fluid cell (Sec. 2.1 evolution equation, pull
+// form): gather, collide, store, refill the ghost slots of its wall links.
+template <int P, bool GHOST1, bool WIDE>
+__global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
+    using R = typename Storage<P>::R;
     const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
     const int chunk = gt / CHUNK;
     double hv[6] = {0, 0, 0, 0, 0, 0};
     if (chunk < a.nchunks) {
         const int2 ch = __ldg(a.chunks + chunk);
-        const int row = ch.x;
-        const int x = ch.y + (gt % CHUNK);
-        const int y = row % a.ny, z = row / a.ny;
-        const int slot = __ldg(a.row_base + row) + x;
-        const uint32_t m = __ldg(a.mask + slot);
-        const uint32_t type = (m >> TYPE_SHIFT) & 3u;
-        if (type != TYPE_PAD) {
+        const uint32_t cw = (uint32_t)ch.y;
+        const int lane = gt % CHUNK;
+        if ((cw >> (CHUNK_LANES_SHIFT + lane)) & 1u) {
+            const int x = (int)(cw & CHUNK_X0_MASK) + lane;
+            int nb[9];
+            load_row(a.row_nb, ch.x, nb);
+            const int slot = nb[4] + x;
+            const uint32_t links = __ldg(a.mask + slot) & LINK_MASK;  // needed after the collision only
             R d[27];
             R rho, ux, uy, uz;
-            const R omega = R(a.omega);
-            R ghost[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) ghost[q] = R(a.ghost[q]);
-            if (type == TYPE_FLUID) {
-                gather<P>(a, x, y, z, slot, m, d);
-                if (GHOST1)
-                    collide_ghost1<R>(d, omega, rho, ux, uy, uz);
-                else
-                    collide_general<R>(d, omega, ghost, rho, ux, uy, uz);
-            } else {
-                const int dir = (int)(m >> DIR_SHIFT);
-                const int nx_ = (dir == 0) - (dir == 1), ny_ = (dir == 2) - (dir == 3), nz_ = (dir == 4) - (dir == 5);
-                const int xf = wrap(x + nx_, a.nx), yf = wrap(y + ny_, a.ny), zf = wrap(z + nz_, a.nz);
-                const int slot_f = __ldg(a.row_base + zf * a.ny + yf) + xf;
-                const uint32_t mf = __ldg(a.mask + slot_f);
-                R rf, uxf, uyf, uzf;
-                gather<P>(a, xf, yf, zf, slot_f, mf, d);
-                if (GHOST1)
-                    collide_ghost1<R>(d, omega, rf, uxf, uyf, uzf);
-                else
-                    collide_general<R>(d, omega, ghost, rf, uxf, uyf, uzf);
-                if (type == TYPE_INLET) {
-                    R speed = R(a.u_in);
-                    if (a.profile == LBM_PROFILE_PARABOLIC) {
-                        const R rx = R(x) + R(0.5) - R(a.axis_x), ry = R(y) + R(0.5) - R(a.axis_y);
-                        const R r2 = rx * rx + ry * ry;
-                        const R din = R(a.d_in);
-                        speed = R(2) * R(a.u_in) * (R(1) - R(4) * r2 / (din * din));
-                    }
-                    rho = rf;
-                    ux = speed * R(nx_);
-                    uy = speed * R(ny_);
-                    uz = speed * R(nz_);
-                    if (a.noise_amp != 0.0) {
-                        const int64_t node = (int64_t)x + (int64_t)a.nx * ((int64_t)y + (int64_t)a.ny * z);
-                        const R amp = R(a.noise_amp) * R(a.u_in);
-                        ux += amp * inlet_noise<R>(a.seed, a.t_new, node, 0);
-                        uy += amp * inlet_noise<R>(a.seed, a.t_new, node, 1);
-                        uz += amp * inlet_noise<R>(a.seed, a.t_new, node, 2);
-                    }
-                } else {
-                    rho = R(a.rho_out);
-                    ux = uxf;
-                    uy = uyf;
-                    uz = uzf;
-                }
-                R eb[27], ef[27];
-                eq_deviation<R>(rho, Axis<R>(ux), Axis<R>(uy), Axis<R>(uz), eb);
-                eq_deviation<R>(rf, Axis<R>(uxf), Axis<R>(uyf), Axis<R>(uzf), ef);
-#pragma unroll
-                for (int i = 0; i < 27; ++i) d[i] += eb[i] - ef[i];
-            }
-            T *fout = static_cast<T *>(a.fout);
-            const R s = R(a.scale);
-#pragma unroll
-            for (int i = 0; i < 27; ++i) S::store(fout + (int64_t)i * a.stride + slot, d[i], s);
-            if (a.flags & STEP_STATS) {
-                const double w = (double)uz;
-                a.stats[slot] += w;
-                a.stats[a.stride + slot] += w * w;
-            }
-            if (a.flags & STEP_REDUCE) health_values(rho, ux, uy, uz, hv);
+            gather<P, WIDE>(a, nb, x, d);
+            collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
+            store_cell_state<P, WIDE>(a, nb, x, slot, links, d);
+            record_cell(a, slot, rho, ux, uy, uz, hv);
         }
     }
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
+}
+
+// One time step of every inlet/outlet node: non-equilibrium extrapolation
+// (Sec. 2.2) from the interior partner x_f, whose update is recomputed here
+// from the same input state (so this kernel and k_step are independent):
+//   f*_i(x_b) = f^eq_i(rho_b, u_b) + f*_i(x_f) - f^eq_i(rho_f, u_f),
+// inlet: rho_b = rho_f, u_b prescribed; outlet: rho_b = rho_out, u_b = u_f.
+template <int P, bool GHOST1, bool WIDE>
+__global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
+    using R = typename Storage<P>::R;
+    const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
+    double hv[6] = {0, 0, 0, 0, 0, 0};
+    if (k < a.nbnodes) {
+        const int4 node = __ldg(a.bnodes + k);
+        const int x = node.x, row = node.y, slot = node.z;
+        const uint32_t m = (uint32_t)node.w;
+        const uint32_t type = (m >> TYPE_SHIFT) & 3u;
+        const FlowParams<R> &fp = flow<R>(a);
+        const int y = row % a.ny_e - 1, z = row / a.ny_e - 1;
+        const int dir = (int)(m >> DIR_SHIFT);
+        const int nx_ = (dir == 0) - (dir == 1), ny_ = (dir == 2) - (dir == 3), nz_ = (dir == 4) - (dir == 5);
+        const int xf = wrap(x + nx_, a.nx), yf = wrap(y + ny_, a.ny), zf = wrap(z + nz_, a.nz);
+        int nbf[9];
+        load_row(a.row_nb, (yf + 1) + a.ny_e * (zf + 1), nbf);
+        R d[27];
+        R rf, uxf, uyf, uzf, rho, ux, uy, uz;
+        gather<P, WIDE>(a, nbf, xf, d);
+        collide<P, GHOST1>(d, fp, rf, uxf, uyf, uzf);
+        if (type == TYPE_INLET) {
+            R speed = fp.u_in;
+            if (a.profile == LBM_PROFILE_PARABOLIC) {
+                const R rx = R(x) + R(0.5) - fp.axis_x, ry = R(y) + R(0.5) - fp.axis_y;
+                const R r2 = rx * rx + ry * ry;
+                speed = R(2) * fp.u_in * (R(1) - R(4) * r2 / (fp.d_in * fp.d_in));
+            }
+            rho = rf;
+            ux = speed * R(nx_);
+            uy = speed * R(ny_);
+            uz = speed * R(nz_);
+            if (fp.noise_amp != R(0)) {
+                const int64_t node_id = (int64_t)x + (int64_t)a.nx * ((int64_t)y + (int64_t)a.ny * z);
+                const R amp = fp.noise_amp * fp.u_in;
+                ux += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 0);
+                uy += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 1);
+                uz += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 2);
+            }
+        } else {
+            rho = fp.rho_out;
+            ux = uxf;
+            uy = uyf;
+            uz = uzf;
+        }
+        add_eq_difference<R>(rho, ux, uy, uz, rf, uxf, uyf, uzf, d);
+        int nb[9];
+        load_row(a.row_nb, row, nb);
+        store_cell_state<P, WIDE>(a, nb, x, slot, 0u, d);
+        record_cell(a, slot, rho, ux, uy, uz, hv);
+    }
+    if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials + (size_t)a.fluid_blocks * REDUCE_SLOTS);
+}
+
+// ------------------------------------------- staged (bulk-copy) step kernel
+
+// PTX wrappers: mbarrier (shared::cta) and 1-D bulk async copy global -> shared.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of a barrier for at most limit_ns; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // 1 s
+constexpr uint32_t STATUS_TIMEOUT = 2u;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int P>
+struct Staging {
+    using T = typename Storage<P>::T;
+    static constexpr int HALO = 16 / (int)sizeof(T);  // elements of 16 bytes: copy alignment
+    static constexpr int W = SEGMENT + 2 * HALO;       // staged row width (elements)
+    static constexpr int MW = SEGMENT + 8;             // staged link words
+    static constexpr size_t POP_BYTES = (size_t)27 * W * sizeof(T);
+    static constexpr size_t BUF_BYTES = (POP_BYTES + (size_t)MW * 4 + 127) & ~(size_t)127;
+    static constexpr size_t SMEM_BYTES = STAGES * BUF_BYTES;
+};
+
+// Segment header staged with each buffer: row, x0, count, nb[9].
+struct SegInfo {
+    int row, x0, count, pad;
+    int nb[9];
+    int pad2[3];
+};
+
+// One time step of every fluid cell, staged and warp-specialised.  Each
+// block walks segments (runs of up to SEGMENT cells of one row).  Its
+// producer warp stages, per segment, the 27 pull rows (population i comes
+// from row j(i) at x - cx, x in [x0 - 1, x0 + count]) and the link words into
+// a ring of STAGES shared-memory buffers with bulk async copies, completing
+// on the buffer's "full" mbarrier; the consumer warps (one thread per cell)
+// wait on "full", collide from shared memory at compile-time offsets, store
+// to global memory, and release the buffer on its "empty" mbarrier.  Every
+// wait is bounded (WAIT_LIMIT_NS); on expiry the kernel raises
+// STATUS_TIMEOUT, lets its own copies land, and returns.
+template <int P, bool GHOST1, bool WIDE>
+__global__ void __launch_bounds__(STAGED_THREADS) k_step_staged(const StepArgs a) {
+    using St = Staging<P>;
+    using S = Storage<P>;
+    using T = typename S::T;
+    using R = typename S::R;
+    constexpr int HALO = St::HALO, W = St::W;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    __shared__ SegInfo info[STAGES];
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < STAGES; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], CONSUMER_WARPS);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane != 0) return;
+        const T *fin = static_cast<const T *>(a.fin);
+        int seg = blockIdx.x;
+        int it = 0;
+        int4 r0 = make_int4(0, 0, 0, 0), r1 = r0, r2 = r0;
+        if (seg < a.nsegs) {
+            r0 = __ldg(a.segs + SEG_RECORD_INT4 * seg);
+            r1 = __ldg(a.segs + SEG_RECORD_INT4 * seg + 1);
+            r2 = __ldg(a.segs + SEG_RECORD_INT4 * seg + 2);
+        }
+        for (; seg < a.nsegs; seg += gridDim.x, ++it) {
+            const int b = it % STAGES;
+            const int next = seg + gridDim.x;  // prefetch the next record while this one is staged
+            int4 n0 = r0, n1 = r1, n2 = r2;
+            if (next < a.nsegs) {
+                n0 = __ldg(a.segs + SEG_RECORD_INT4 * next);
+                n1 = __ldg(a.segs + SEG_RECORD_INT4 * next + 1);
+                n2 = __ldg(a.segs + SEG_RECORD_INT4 * next + 2);
+            }
+            if (it >= STAGES && !mbar_wait_bounded(&empty[b], (uint32_t)(it / STAGES - 1) & 1u, WAIT_LIMIT_NS)) {
+                atomicOr(a.status, STATUS_TIMEOUT);
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (*(volatile int *)&abort_flag) break;
+            SegInfo &in = info[b];
+            const int nb[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r0.w};
+            in.row = r0.x;
+            in.x0 = r0.y;
+            in.count = r0.z;
+#pragma unroll
+            for (int j = 0; j < 9; ++j) in.nb[j] = nb[j];
+            const int n_el = ((r0.z + 2 * HALO + HALO - 1) / HALO) * HALO;  // multiple of 16 bytes
+            const int n_mask = ((r0.z + 8 + 3) / 4) * 4;
+            const uint32_t pop_bytes = (uint32_t)(n_el * (int)sizeof(T));
+            mbar_arrive_expect_tx(&full[b], 27u * pop_bytes + (uint32_t)n_mask * 4u);
+            T *dst = reinterpret_cast<T *>(smem + b * St::BUF_BYTES);
+#pragma unroll
+            for (int i = 0; i < 27; ++i)
+                bulk_copy_g2s(dst + i * W, fin + ((int64_t)i * a.stride + nb[i / 3] + r0.y - HALO), pop_bytes, &full[b]);
+            bulk_copy_g2s(smem + b * St::BUF_BYTES + St::POP_BYTES, a.mask + (nb[4] + r0.y - 4), (uint32_t)n_mask * 4u,
+                          &full[b]);
+            r0 = n0;
+            r1 = n1;
+            r2 = n2;
+        }
+        // let every copy issued by this block land before leaving
+        const int last = it < STAGES ? it : STAGES;
+        for (int k = 1; k <= last; ++k) {
+            const int u = it - k;  // use index of the buffer's last stage
+            mbar_wait_bounded(&full[u % STAGES], (uint32_t)(u / STAGES) & 1u, WAIT_LIMIT_NS);
+        }
+        return;
+    }
+
+    // --------------------------------------------------------------- consumers
+    const int t = threadIdx.x - 32;  // cell lane within the segment
+    double hv[6] = {0, 0, 0, 0, 0, 0};
+    const R inv_s = R(a.inv_scale);
+    int it = 0;
+    for (int seg = blockIdx.x; seg < a.nsegs; seg += gridDim.x, ++it) {
+        const int b = it % STAGES;
+        if (!mbar_wait_bounded(&full[b], (uint32_t)(it / STAGES) & 1u, WAIT_LIMIT_NS)) {
+            if (lane == 0) {
+                atomicOr(a.status, STATUS_TIMEOUT);
+                atomicExch(&abort_flag, 1);
+            }
+            break;
+        }
+        const SegInfo &in = info[b];
+        if (t < in.count) {
+            const uint32_t *mw = reinterpret_cast<const uint32_t *>(smem + b * St::BUF_BYTES + St::POP_BYTES);
+            const uint32_t m = mw[t + 4];
+            if (((m >> TYPE_SHIFT) & 3u) == TYPE_FLUID) {
+                const T *src = reinterpret_cast<const T *>(smem + b * St::BUF_BYTES) + t + HALO;
+                R d[27];
+#pragma unroll
+                for (int i = 0; i < 27; ++i) d[i] = S::load_shared(src + i * W - cx_of(i), inv_s);
+                int nb[9];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) nb[j] = in.nb[j];
+                const int x = in.x0 + t;
+                const int slot = nb[4] + x;
+                R rho, ux, uy, uz;
+                collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
+                store_cell_state<P, WIDE>(a, nb, x, slot, m & LINK_MASK, d);
+                record_cell(a, slot, rho, ux, uy, uz, hv);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+        if (*(volatile int *)&abort_flag) break;
+    }
+    if (a.flags & STEP_REDUCE) {  // one partial per consumer warp, fixed order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const double v = __shfl_down_sync(0xffffffffu, hv[k], o);
+                hv[k] = (k == 4) ? fmax(hv[k], v) : hv[k] + v;
+            }
+        if (lane == 0) {
+            double *p = a.partials + ((size_t)blockIdx.x * CONSUMER_WARPS + (warp - 1)) * REDUCE_SLOTS;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) p[k] = hv[k];
+        }
+    }
 }
 
 // ---------------------------------------------------------- utility kernels
@@ -500,23 +828,70 @@ __device__ __forceinline__ void moments_of(const double (&d)[27], double &rho, d
 
 // Health reduction of a stored state (mass, momentum, max |u|, non-finite count).
 template <int P>
-__global__ void __launch_bounds__(STEP_THREADS) k_reduce(const void *f, const uint32_t *mask, const int2 *chunks,
-                                                         const int32_t *row_base, int32_t nchunks, int64_t stride,
-                                                         float inv_scale, double *partials) {
-    const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
-    const int chunk = gt / CHUNK;
+__global__ void __launch_bounds__(STEP_THREADS) k_reduce(const void *f, const int32_t *slot_of_active, int64_t n,
+                                                         int64_t stride, float inv_scale, double *partials) {
+    const int64_t k = (int64_t)blockIdx.x * STEP_THREADS + threadIdx.x;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (chunk < nchunks) {
-        const int2 ch = chunks[chunk];
-        const int slot = row_base[ch.x] + ch.y + gt % CHUNK;
-        if (((mask[slot] >> TYPE_SHIFT) & 3u) != TYPE_PAD) {
-            double d[27], rho, ux, uy, uz;
-            load_cell<P>(f, stride, slot, inv_scale, d);
-            moments_of(d, rho, ux, uy, uz);
-            health_values(rho, ux, uy, uz, hv);
-        }
+    if (k < n) {
+        double d[27], rho, ux, uy, uz;
+        load_cell<P>(f, stride, slot_of_active[k], inv_scale, d);
+        moments_of(d, rho, ux, uy, uz);
+        health_values(rho, ux, uy, uz, hv);
     }
     block_reduce_write(hv, partials);
+}
+
+// Ghost slots and periodic-x copies of one buffer from its active cells:
+// the same writes the step kernel does after its collision, for a state set
+// from the host.
+template <int P>
+__global__ void __launch_bounds__(STEP_THREADS) k_fill_ghosts(void *f, const uint32_t *mask, const int2 *chunks,
+                                                              const int4 *row_nb, int32_t nchunks, int64_t stride,
+                                                              int32_t nx, int32_t periodic_x) {
+    using T = typename Storage<P>::T;
+    const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
+    const int chunk = gt / CHUNK;
+    if (chunk >= nchunks) return;
+    const int2 ch = chunks[chunk];
+    const uint32_t cw = (uint32_t)ch.y;
+    const int lane = gt % CHUNK;
+    if (!((cw >> (CHUNK_LANES_SHIFT + lane)) & 1u)) return;
+    const int x = (int)(cw & CHUNK_X0_MASK) + lane;
+    int nb[9];
+    load_row(row_nb, ch.x, nb);
+    const int slot = nb[4] + x;
+    T *p = static_cast<T *>(f);
+    const uint32_t links = mask[slot] & LINK_MASK;
+#pragma unroll
+    for (int i = 0; i < 27; ++i)
+        if (links & (1u << i)) p[(int64_t)i * stride + nb[i / 3] + x - cx_of(i)] = p[(int64_t)(26 - i) * stride + slot];
+    if (periodic_x) {
+        if (x == nx - 1)
+#pragma unroll
+            for (int i = 2; i < 27; i += 3) p[(int64_t)i * stride + nb[4] - 1] = p[(int64_t)i * stride + slot];
+        if (x == 0)
+#pragma unroll
+            for (int i = 0; i < 27; i += 3) p[(int64_t)i * stride + nb[4] + nx] = p[(int64_t)i * stride + slot];
+    }
+}
+
+// Periodic-x copies of the inlet/outlet nodes.
+template <int P>
+__global__ void __launch_bounds__(STEP_THREADS) k_fill_periodic_nodes(void *f, const int4 *bnodes, int32_t nbnodes,
+                                                                      const int4 *row_nb, int64_t stride, int32_t nx) {
+    using T = typename Storage<P>::T;
+    const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
+    if (k >= nbnodes) return;
+    const int4 node = bnodes[k];
+    const int x = node.x, slot = node.z;
+    const int base = row_nb[3 * node.y + 1].x;
+    T *p = static_cast<T *>(f);
+    if (x == nx - 1)
+#pragma unroll
+        for (int i = 2; i < 27; i += 3) p[(int64_t)i * stride + base - 1] = p[(int64_t)i * stride + slot];
+    if (x == 0)
+#pragma unroll
+        for (int i = 0; i < 27; i += 3) p[(int64_t)i * stride + base + nx] = p[(int64_t)i * stride + slot];
 }
 
 template <int P>
@@ -591,23 +966,90 @@ inline int step_blocks(int32_t nchunks) {
     return (int)((threads + STEP_THREADS - 1) / STEP_THREADS);
 }
 
+#ifndef LBM_STAGED
+#define LBM_STAGED 0
+#endif
+
+template <int P, bool G, bool WD>
+int staged_grid(int device) {
+    static int per_sm[64] = {0};
+    static int sms[64] = {0};
+    if (device < 0 || device >= 64) device = 0;
+    if (per_sm[device] == 0) {
+        cudaFuncSetAttribute(k_step_staged<P, G, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Staging<P>::SMEM_BYTES);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_staged<P, G, WD>, STAGED_THREADS,
+                                                      Staging<P>::SMEM_BYTES);
+        cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
+        per_sm[device] = n > 0 ? n : 1;
+    }
+    return per_sm[device] * sms[device];
+}
+
+// Grid of the staged kernel (persistent blocks, at most one per segment).
+template <int P>
+int staged_blocks(int32_t nsegs, int device) {
+    const int g = std::max(std::max(staged_grid<P, true, false>(device), staged_grid<P, false, false>(device)),
+                           std::max(staged_grid<P, true, true>(device), staged_grid<P, false, true>(device)));
+    return std::max(1, std::min(nsegs, g));
+}
+
+// Partial-sum slots written by the fluid kernel of one step.
+template <int P>
+int step_fluid_blocks(int32_t nchunks, int32_t nsegs, int device) {
+    if (!LBM_STAGED) return step_blocks(nchunks);
+    return staged_blocks<P>(nsegs, device) * CONSUMER_WARPS;
+}
+
+template <int P, bool G, bool WD>
+void launch_fluid(const StepArgs &a, cudaStream_t s) {
+    if (LBM_STAGED) {
+        const int grid = a.fluid_blocks / CONSUMER_WARPS;
+        k_step_staged<P, G, WD><<<grid, STAGED_THREADS, Staging<P>::SMEM_BYTES, s>>>(a);
+    } else {
+        k_step<P, G, WD><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
+    }
+}
+
 template <int P>
 cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s) {
-    const int blocks = step_blocks(a.nchunks);
-    if (blocks == 0) return cudaSuccess;
-    if (ghost1)
-        k_step<P, true><<<blocks, STEP_THREADS, 0, s>>>(a);
-    else
-        k_step<P, false><<<blocks, STEP_THREADS, 0, s>>>(a);
+    const bool wide = a.stride > MAX_SLOTS_32;
+    const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
+    if (a.nsegs > 0) {
+        if (ghost1)
+            wide ? launch_fluid<P, true, true>(a, s) : launch_fluid<P, true, false>(a, s);
+        else
+            wide ? launch_fluid<P, false, true>(a, s) : launch_fluid<P, false, false>(a, s);
+    }
+    if (bb > 0) {
+        if (ghost1)
+            wide ? k_boundary<P, true, true><<<bb, STEP_THREADS, 0, s>>>(a) : k_boundary<P, true, false><<<bb, STEP_THREADS, 0, s>>>(a);
+        else
+            wide ? k_boundary<P, false, true><<<bb, STEP_THREADS, 0, s>>>(a) : k_boundary<P, false, false><<<bb, STEP_THREADS, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t launch_reduce(const void *f, const uint32_t *mask, const int2 *chunks, const int32_t *row_base,
-                          int32_t nchunks, int64_t stride, float inv_scale, double *partials, cudaStream_t s) {
-    const int blocks = step_blocks(nchunks);
+cudaError_t launch_reduce(const void *f, const int32_t *slot_of_active, int64_t n, int64_t stride, float inv_scale,
+                          double *partials, cudaStream_t s) {
+    const int blocks = (int)((n + STEP_THREADS - 1) / STEP_THREADS);
     if (blocks == 0) return cudaSuccess;
-    k_reduce<P><<<blocks, STEP_THREADS, 0, s>>>(f, mask, chunks, row_base, nchunks, stride, inv_scale, partials);
+    k_reduce<P><<<blocks, STEP_THREADS, 0, s>>>(f, slot_of_active, n, stride, inv_scale, partials);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_fill_ghosts(void *f, const uint32_t *mask, const int2 *chunks, const int4 *row_nb,
+                               int32_t nchunks, const int4 *bnodes, int32_t nbnodes, int64_t stride, int32_t nx,
+                               int32_t periodic_x, cudaStream_t s) {
+    const int blocks = step_blocks(nchunks);
+    if (blocks > 0)
+        k_fill_ghosts<P><<<blocks, STEP_THREADS, 0, s>>>(f, mask, chunks, row_nb, nchunks, stride, nx, periodic_x);
+    if (periodic_x && nbnodes > 0)
+        k_fill_periodic_nodes<P><<<(nbnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(
+            f, bnodes, nbnodes, row_nb, stride, nx);
     return cudaGetLastError();
 }
 
@@ -647,8 +1089,11 @@ cudaError_t launch_init_eq(void *f, const int32_t *soa, int64_t n, int64_t strid
 
 #define LBM_INSTANTIATE(P)                                                                                         \
     template cudaError_t launch_step<P>(const StepArgs &, bool, cudaStream_t);                                     \
-    template cudaError_t launch_reduce<P>(const void *, const uint32_t *, const int2 *, const int32_t *, int32_t, \
-                                          int64_t, float, double *, cudaStream_t);                                 \
+    template int step_fluid_blocks<P>(int32_t, int32_t, int);                                                       \
+    template cudaError_t launch_reduce<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \
+                                          cudaStream_t);                                                           \
+    template cudaError_t launch_fill_ghosts<P>(void *, const uint32_t *, const int2 *, const int4 *, int32_t,      \
+                                               const int4 *, int32_t, int64_t, int32_t, int32_t, cudaStream_t);    \
     template cudaError_t launch_moments<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \
                                            cudaStream_t);                                                          \
     template cudaError_t launch_get_populations<P>(const void *, const int32_t *, int64_t, int64_t, float,         \

@@ -17,14 +17,29 @@ namespace lbm {
 // that chunk lanes map to consecutive, aligned storage slots.
 constexpr int CHUNK = 8;
 constexpr int STEP_THREADS = 256;
+// Staged step kernel: a segment is a run of at most SEGMENT fluid-row cells
+// starting on a CHUNK boundary; its 27 pull rows are staged in shared memory
+// by bulk async copies.  Each block has one producer warp and
+// SEGMENT / 32 consumer warps (one thread per cell) sharing a ring of
+// STAGES staged segments.
+constexpr int SEGMENT = 64;
+constexpr int CONSUMER_WARPS = SEGMENT / 32;
+constexpr int STAGED_THREADS = 32 * (1 + CONSUMER_WARPS);
+constexpr int STAGES = 3;
+// Segment record: 3 x int4 = {row, x0, count, nb[8]}, nb[0..3], nb[4..7].
+constexpr int SEG_RECORD_INT4 = 3;
 constexpr int REDUCE_SLOTS = 8;  // doubles per block partial
 
 // Per-slot link word.
-//   bits 0..26 : population i must bounce back (its pull source x - c_i is a
-//                wall or outside a non-periodic face)
-//   bits 27..28: node type (0 fluid, 1 inlet, 2 outlet, 3 padding)
+//   bits 0..26 : link i is a wall link: the pull source x - c_i is solid or
+//                outside a non-periodic face.  The cell then writes its
+//                reflected population f*_{26-i} into the ghost slot that
+//                stands at x - c_i in population array i, so that the next
+//                step's pull of population i is the halfway bounce-back.
+//   bits 27..28: node type (0 fluid, 1 inlet, 2 outlet, 3 padding / ghost)
 //   bits 29..31: inlet/outlet partner direction (0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z)
 enum : uint32_t {
+    LINK_MASK = (1u << 27) - 1u,
     TYPE_SHIFT = 27,
     TYPE_FLUID = 0,
     TYPE_INLET = 1,
@@ -35,34 +50,76 @@ enum : uint32_t {
 
 enum : int { STEP_REDUCE = 1, STEP_STATS = 2 };
 
+// Chunk records (int2): x = row, y = x0 | fluid-lane mask << CHUNK_LANES_SHIFT.
+// The lane mask lets the gather start without waiting for the per-cell link
+// words.  Inlet/outlet nodes are not in chunks: a separate boundary-node list
+// (int4: x, row, slot, link word) drives the boundary kernel.
+enum : uint32_t {
+    CHUNK_X0_MASK = (1u << 20) - 1u,
+    CHUNK_LANES_SHIFT = 20,
+};
+
+// Row records: rows are indexed over the box extended by one ghost layer in
+// y and z, row = (y + 1) + (ny + 2) (z + 1).  Each row record holds the
+// storage bases of the nine neighbour rows (y - cy, z - cz), j = (cy + 1) +
+// 3 (cz + 1), so that the slot of the pull source of population i of cell x
+// is nb[j] + x - cx for every link (j = 4 is the row itself).
+constexpr int ROW_RECORD_INTS = 12;
+
+// Flow parameters in the arithmetic precision of a kernel.
+template <class R>
+struct FlowParams {
+    R omega;
+    R ghost[4];
+    R u_in, d_in, axis_x, axis_y, noise_amp, rho_out;
+};
+
 struct StepArgs {
-    const void *fin;
+    const void *fin;        // population arrays [27][stride], storage type of the kernel
     void *fout;
     const uint32_t *mask;
-    const int32_t *row_base;
-    const int2 *chunks;  // (row = y + ny z, x0)
-    int64_t stride;      // elements between two populations (= slot count)
+    const int4 *row_nb;     // [rows][3] row records
+    const int2 *chunks;     // chunk records (fluid cells)
     int32_t nchunks;
-    int32_t nx, ny, nz;
-    int32_t flags;       // STEP_REDUCE | STEP_STATS
+    const int4 *bnodes;     // boundary nodes (x, row, slot, link word)
+    int32_t nbnodes;
+    int32_t fluid_blocks;   // blocks of the fluid kernel (offset of the boundary kernel's partials)
+    const int4 *segs;       // segment records of fluid cells (SEG_RECORD_INT4 int4 each)
+    int32_t nsegs;
+    uint32_t *status;       // bit 1: a bounded device wait gave up
+    int32_t nx, ny, nz, ny_e;
+    int32_t flags;          // STEP_REDUCE | STEP_STATS
     int32_t profile;
-    double omega;
-    double ghost[4];
-    double u_in, d_in, axis_x, axis_y, noise_amp, rho_out;
+    int32_t periodic_x;
+    FlowParams<double> pd;
+    FlowParams<float> pf;
     uint64_t seed;
     int64_t t_new;
     float scale, inv_scale;
-    double *stats;       // [2][stride]: sum u_z, sum u_z^2
-    double *partials;    // [gridDim.x][REDUCE_SLOTS]
+    int64_t stride;         // elements between two population arrays (= slot count)
+    double *stats;          // [2][stride]: sum u_z, sum u_z^2
+    double *partials;       // [gridDim.x][REDUCE_SLOTS]
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).
+// Offsets into a population buffer fit in 32 bits (unsigned) when
+// 27 * slots < 2^32; larger lattices use 64-bit offsets.
+constexpr int64_t MAX_SLOTS_32 = (int64_t)0xFFFFFFFFu / 27 - 64;
+
 template <int P>
 cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s);
+// Blocks of one step's fluid kernel (partial-sum slots it writes).
 template <int P>
-cudaError_t launch_reduce(const void *f, const uint32_t *mask, const int2 *chunks,
-                          const int32_t *row_base, int32_t nchunks, int64_t stride, float inv_scale,
+int step_fluid_blocks(int32_t nchunks, int32_t nsegs, int device);
+template <int P>
+cudaError_t launch_reduce(const void *f, const int32_t *slot_of_active, int64_t n, int64_t stride, float inv_scale,
                           double *partials, cudaStream_t s);
+// Write the bounce-back ghost slots and periodic-x copies of buffer f from
+// its active cells (after any host-side change of the state).
+template <int P>
+cudaError_t launch_fill_ghosts(void *f, const uint32_t *mask, const int2 *chunks, const int4 *row_nb,
+                               int32_t nchunks, const int4 *bnodes, int32_t nbnodes, int64_t stride, int32_t nx,
+                               int32_t periodic_x, cudaStream_t s);
 template <int P>
 cudaError_t launch_moments(const void *f, const int32_t *slot_of_active, int64_t n, int64_t stride,
                            float inv_scale, double *out4, cudaStream_t s);
@@ -77,7 +134,8 @@ cudaError_t launch_init_eq(void *f, const int32_t *slot_of_active, int64_t n, in
                            float scale, const double *rho, const double *u, double rho0,
                            double ux, double uy, double uz, cudaStream_t s);
 
-int reduce_blocks(int32_t nchunks);
+int fluid_blocks(int32_t nchunks);
+int node_blocks(int64_t n);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *health, uint32_t *status,
                             cudaStream_t s);
 cudaError_t launch_stats_mean(const double *stats, const int32_t *slot_of_active, int64_t n,
@@ -87,14 +145,26 @@ cudaError_t launch_stats_mean(const double *stats, const int32_t *slot_of_active
 struct HostIndex {
     int64_t n_active = 0;
     int64_t nslots = 0;
-    std::vector<int32_t> row_base;        // [ny*nz]
-    std::vector<int2> chunks;             // (row, x0)
+    int64_t n_ghost = 0;                  // bounce-back ghost slots
+    int32_t ny_e = 0, nz_e = 0;           // extended row grid
+    std::vector<int32_t> row_nb;          // [rows][ROW_RECORD_INTS]
+    std::vector<int2> chunks;             // chunk records (fluid cells)
+    std::vector<int4> bnodes;             // inlet/outlet nodes: x, row, slot, link word
+    std::vector<int4> segs;               // segment records (SEG_RECORD_INT4 int4 each)
     std::vector<uint32_t> mask;           // [nslots]
     std::vector<int32_t> slot_of_active;  // [n_active], active order = increasing box index
     std::vector<int64_t> box_of_active;   // [n_active]
 };
 
+// Margin (elements) kept readable before and after every population buffer
+// and (in link words) around the link-word array, so that the staged
+// kernel's aligned row copies never leave the allocation.
+inline int64_t buffer_margin(int nx) { return ((int64_t)nx + SEGMENT + 64 + 63) & ~(int64_t)63; }
+constexpr int64_t MASK_MARGIN = 64;
+
 // Returns "" on success, else a description of the inconsistency.
 std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out);
+// Independent check of the index invariants the kernels rely on ("" if all hold).
+std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, int ny, int nz, int periodic);
 
 }  // namespace lbm

@@ -75,6 +75,8 @@ _SIGS = {
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_make_nozzle": (C.c_int, [C.c_int32] * 6 + [C.c_double, C.c_void_p]),
+    "lbm_check_layout": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                   C.POINTER(C.c_int64)]),
     "lbm_set_geometry": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_fluid_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "lbm_set_params": (C.c_int, [C.c_void_p, C.POINTER(lbm_params)]),
@@ -134,6 +136,19 @@ def make_nozzle(D, d, L_total, L_in=None, L_cone=-1, L_throat=None, half_angle_d
     if st != LBM_OK:
         raise LbmError(st, "lbm_make_nozzle")
     return out
+
+
+def check_layout(flags, periodic=0):
+    """lbm_check_layout: host-only index build + invariant check.  Returns a
+    dict of counts; raises LbmError on an inconsistent field or index."""
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    nz, ny, nx = flags.shape
+    out = (C.c_int64 * 8)()
+    st = capi().lbm_check_layout(flags.ctypes.data, nx, ny, nz, int(periodic), out)
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_check_layout")
+    keys = ["active", "slots", "segments", "chunks", "boundary_nodes", "wall_links", "rows"]
+    return dict(zip(keys, list(out)[:7]))
 
 
 class TorchAllocator:

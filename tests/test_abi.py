@@ -75,3 +75,61 @@ def test_create_rejects_bad_descriptors(lib):
     d.precision, d.fp16_scale = 2, 3.0   # not a power of two
     assert lib.lbm_create(C.byref(d), C.byref(ctx)) == lbm.LBM_ERR_ARG
     assert lib.lbm_destroy(None) == lbm.LBM_OK
+
+
+def _ragged():
+    g = np.random.default_rng(12)
+    f = np.ones((9, 11, 37), dtype=np.uint8)
+    f[:, :, :3] = 0
+    f[:, 4:7, 15:18] = 0
+    f[2:4, 1, 30:] = 0
+    f[g.random(f.shape) < 0.03] = 0
+    return f
+
+
+def _duct(n, nz, nx=None):
+    f = np.ones((nz, n, nx or n), dtype=np.uint8)
+    f[0] = 2
+    f[-1] = 3
+    return f
+
+
+@pytest.mark.parametrize("case", ["nozzle", "ragged", "box13", "box70", "duct", "pipe", "long_rows"])
+@pytest.mark.parametrize("periodic", [0, 7, 3])
+def test_layout_invariants(lib, case, periodic):
+    """The sparse index the kernels use: every staged copy aligned and in
+    bounds, every fluid cell in exactly one work unit, every pull stored
+    (checked on the host, independently of how the index was built)."""
+    if case == "nozzle":
+        f = I.workload_flags("nozzle_re500_24x24x160")
+    elif case == "ragged":
+        f = _ragged()
+    elif case == "box13":
+        f = np.ones((5, 6, 13), dtype=np.uint8)
+    elif case == "box70":
+        f = np.ones((3, 4, 70), dtype=np.uint8)
+    elif case == "duct":
+        f = _duct(8, 12)
+    elif case == "pipe":
+        f = I.pipe_flags(18, 30)
+    else:
+        f = np.ones((2, 3, 300), dtype=np.uint8)
+        f[:, :, 131:140] = 0
+    if periodic and case in ("nozzle", "pipe"):
+        pytest.skip("walls of the nozzle need no periodic faces")
+    if case == "duct" and periodic & 4:
+        pytest.skip("inlet/outlet planes need a non-periodic z")
+    info = lbm.check_layout(f, periodic)
+    assert info["active"] == int((f != 0).sum())
+    assert info["boundary_nodes"] == int(((f == 2) | (f == 3)).sum())
+    assert info["segments"] >= 1 and info["slots"] % 64 == 0
+
+
+def test_layout_rejects_inconsistent_fields(lib):
+    bad = np.ones((4, 4, 4), dtype=np.uint8)
+    bad[0, 0, 0] = 2
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.check_layout(bad)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError):
+        lbm.check_layout(np.zeros((2, 2, 2), dtype=np.uint8))
