@@ -95,6 +95,14 @@ def recorded_traffic(workload, precision):
     return None
 
 
+def launches_per_step(flags, periodic):
+    """Kernels one lattice step launches: the fluid kernel, plus the
+    inlet/outlet kernel when the geometry has such nodes."""
+    from paper_2204_10566_gb300 import lbm
+
+    return 1 + (1 if lbm.check_layout(flags, periodic)["boundary_nodes"] > 0 else 0)
+
+
 class ClockSampler:
     """nvidia-smi SM clock / throttle-reason samples during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -369,7 +377,7 @@ def ours_arm(args):
                      "bytes_per_cell": algorithmic_bytes_per_cell(head)},
         "by_precision": by_prec,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step(flags, periodic),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
