@@ -237,6 +237,35 @@ lbm_status lbm_checkpoint_size(lbm_ctx *ctx, size_t *bytes);
 lbm_status lbm_checkpoint(lbm_ctx *ctx, void *buf, size_t bytes);
 lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes);
 
+/* Largest cell count lbm_totals_noalloc accepts (set by its static scratch). */
+#define LBM_NOALLOC_MAX_CELLS 16777216
+
+/* FP64 totals of a caller-owned population array, allocating nothing.
+ * The paper has no counterpart: this is a service for callers that cannot let
+ * the library allocate device memory -- applications whose device memory
+ * belongs to their own pool and fixed budget, and latency-critical loops in
+ * which cudaMalloc / cudaFree would synchronise the device.  Nothing is
+ * allocated: no cudaMalloc, no cudaFree, no allocator callback.
+ *   f:      DEVICE pointer to the populations in this library's storage form:
+ *           array i at f + i * stride elements, cells 0 .. n-1 contiguous,
+ *           each element f_i - w_i (FP64 / FP32) or (f_i - w_i) * fp16_scale
+ *           as an FP16 (FP16S; fp16_scale 0 selects 4096).
+ *   n:      cells, 1 <= n <= LBM_NOALLOC_MAX_CELLS; stride >= n.
+ *   out:    DEVICE pointer to 6 doubles, written with: mass sum rho, momentum
+ *           sum rho u (3), max |u|, count of non-finite cells.
+ *   stream: cudaStream_t (NULL: default stream); the call only enqueues work.
+ * The per-block partial sums live in one static device array (256 KB) that
+ * every GPU which loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  All calls share
+ * the array: calls whose work overlaps on the GPU (e.g. on two streams) race
+ * and must be serialised by the caller.  Every call overwrites all the
+ * partials it reads, so nothing needs clearing between calls.
+ * Errors: LBM_ERR_ARG (NULL pointer, n out of range, stride < n, bad
+ * precision or scale), LBM_ERR_CUDA. */
+lbm_status lbm_totals_noalloc(const void *f, int32_t precision, float fp16_scale, int64_t n, int64_t stride,
+                              double *out, void *stream);
+
 /* Layout facts for measurement: number of storage slots (active cells plus
  * row padding), bytes of one population buffer, device bytes held. */
 lbm_status lbm_layout_info(lbm_ctx *ctx, int64_t *slots, int64_t *buffer_bytes, int64_t *device_bytes);

@@ -100,6 +100,8 @@ _SIGS = {
     "lbm_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lbm_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lbm_layout_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lbm_totals_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.c_int64, C.c_int64, C.c_void_p,
+                                     C.c_void_p]),
 }
 
 
