@@ -26,7 +26,6 @@ struct lbm_ctx {
     int cur = 0;
     uint32_t *d_mask = nullptr;           // link words (inside d_mask_raw)
     uint32_t *d_mask_raw = nullptr;
-    int4 *d_segs = nullptr;
     int4 *d_row_nb = nullptr;
     int2 *d_chunks = nullptr;
     int4 *d_bnodes = nullptr;
@@ -114,7 +113,6 @@ void release_geometry(lbm_ctx *c) {
     dev_free(c, c->f_raw[0], raw_pop_bytes(c));
     dev_free(c, c->f_raw[1], raw_pop_bytes(c));
     dev_free(c, c->d_mask_raw, raw_mask_bytes(c));
-    dev_free(c, c->d_segs, c->idx.segs.size() * 16);
     dev_free(c, c->d_row_nb, c->idx.row_nb.size() * 4);
     dev_free(c, c->d_chunks, c->idx.chunks.size() * 8);
     dev_free(c, c->d_bnodes, c->idx.bnodes.size() * 16);
@@ -126,7 +124,6 @@ void release_geometry(lbm_ctx *c) {
     c->f[0] = c->f[1] = nullptr;
     c->f_raw[0] = c->f_raw[1] = nullptr;
     c->d_mask = c->d_mask_raw = nullptr;
-    c->d_segs = nullptr;
     c->d_row_nb = nullptr;
     c->d_chunks = nullptr;
     c->d_bnodes = nullptr;
@@ -257,8 +254,7 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     release_geometry(c);
     c->idx = std::move(idx);
     const size_t ns = (size_t)c->idx.nslots;
-    c->fluid_blocks = DISPATCH(c->desc.precision, step_fluid_blocks, (int32_t)c->idx.chunks.size(),
-                               (int32_t)(c->idx.segs.size() / SEG_RECORD_INT4), c->desc.device);
+    c->fluid_blocks = DISPATCH(c->desc.precision, step_fluid_blocks, (int32_t)c->idx.chunks.size());
     c->step_blocks = c->fluid_blocks + node_blocks((int64_t)c->idx.bnodes.size());
     c->nblocks = std::max(c->step_blocks, node_blocks(c->idx.n_active));
     for (int k = 0; k < 2; ++k) {
@@ -267,7 +263,6 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     }
     c->d_mask_raw = (uint32_t *)dev_alloc(c, raw_mask_bytes(c));
     c->d_mask = c->d_mask_raw ? c->d_mask_raw + MASK_MARGIN : nullptr;
-    c->d_segs = (int4 *)dev_alloc(c, c->idx.segs.size() * 16);
     c->d_row_nb = (int4 *)dev_alloc(c, c->idx.row_nb.size() * 4);
     c->d_chunks = (int2 *)dev_alloc(c, c->idx.chunks.size() * 8);
     c->d_bnodes = (int4 *)dev_alloc(c, c->idx.bnodes.size() * 16);
@@ -275,16 +270,13 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     c->d_partials = (double *)dev_alloc(c, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     c->d_health = (double *)dev_alloc(c, 8 * 8);
     c->d_status = (uint32_t *)dev_alloc(c, 256);
-    if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_nb || !c->d_chunks || !c->d_bnodes || !c->d_segs || !c->d_slot_of_active ||
+    if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_nb || !c->d_chunks || !c->d_bnodes || !c->d_slot_of_active ||
         !c->d_partials || !c->d_health || !c->d_status) {
         release_geometry(c);
         return fail(c, LBM_ERR_OOM, "device allocation failed in lbm_set_geometry");
     }
     CK(cudaMemsetAsync(c->d_mask_raw, 0, raw_mask_bytes(c), c->stream), "clear link words");
     CK(cudaMemcpyAsync(c->d_mask, c->idx.mask.data(), ns * 4, cudaMemcpyHostToDevice, c->stream), "copy mask");
-    if (!c->idx.segs.empty())
-        CK(cudaMemcpyAsync(c->d_segs, c->idx.segs.data(), c->idx.segs.size() * 16, cudaMemcpyHostToDevice, c->stream),
-           "copy segments");
     CK(cudaMemcpyAsync(c->d_row_nb, c->idx.row_nb.data(), c->idx.row_nb.size() * 4, cudaMemcpyHostToDevice,
                        c->stream),
        "copy row records");
@@ -471,8 +463,6 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
     a.bnodes = c->d_bnodes;
     a.nbnodes = (int32_t)c->idx.bnodes.size();
     a.fluid_blocks = c->fluid_blocks;
-    a.segs = c->d_segs;
-    a.nsegs = (int32_t)(c->idx.segs.size() / SEG_RECORD_INT4);
     a.status = c->d_status;
     a.nx = c->desc.nx;
     a.ny = c->desc.ny;

@@ -112,12 +112,6 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                 out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(yy, zz)];
             }
             if (act_lo[r] == INT_MAX) continue;
-            const int32_t *nbr = &out.row_nb[(size_t)r * ROW_RECORD_INTS];
-            for (int x0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; x0 <= act_hi[r]; x0 += SEGMENT) {
-                out.segs.push_back(make_int4((int)r, x0, std::min(SEGMENT, act_hi[r] + 1 - x0), nbr[8]));
-                out.segs.push_back(make_int4(nbr[0], nbr[1], nbr[2], nbr[3]));
-                out.segs.push_back(make_int4(nbr[4], nbr[5], nbr[6], nbr[7]));
-            }
             for (int x0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; x0 <= act_hi[r]; x0 += CHUNK) {
                 uint32_t lanes = 0;
                 for (int l = 0; l < CHUNK; ++l) {
@@ -182,45 +176,15 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
 std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, int ny, int nz, int periodic) {
     const int64_t ns = ix.nslots;
     const int64_t nrows = (int64_t)ix.ny_e * ix.nz_e;
-    if (ix.segs.size() % SEG_RECORD_INT4) return "segment records are not whole";
     if (ix.row_nb.size() != (size_t)nrows * ROW_RECORD_INTS) return "row record count";
-    const int64_t margin = buffer_margin(nx);
     std::vector<uint8_t> seen((size_t)nx * ny * nz, 0);
-    for (size_t k = 0; k < ix.segs.size(); k += SEG_RECORD_INT4) {
-        const int4 h = ix.segs[k], a = ix.segs[k + 1], b = ix.segs[k + 2];
-        const int nb[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, h.w};
-        const int r = h.x, x0 = h.y, count = h.z;
-        if (r < 0 || r >= nrows || x0 < 0 || x0 % CHUNK || count < 1 || count > SEGMENT || x0 + count > nx)
-            return "bad segment header";
-        const int y = r % ix.ny_e - 1, z = r / ix.ny_e - 1;
-        if (y < 0 || y >= ny || z < 0 || z >= nz) return "segment row outside the box";
-        for (int j = 0; j < 9; ++j)
-            if (nb[j] != ix.row_nb[(size_t)r * ROW_RECORD_INTS + j] || nb[j] % CHUNK) return "segment row bases";
-        for (int S = 2; S <= 8; S *= 2) {  // FP16, FP32, FP64 element sizes
-            const int halo = 16 / S;
-            const int64_t n_el = ((count + 2 * halo + halo - 1) / halo) * halo;
-            for (int i = 0; i < 27; ++i) {
-                const int64_t start = (int64_t)i * ns + nb[i / 3] + x0 - halo;
-                if ((start * S) % 16) return "staged copy not 16-byte aligned";
-                if (start < -margin || start + n_el > 27 * ns + margin) return "staged copy leaves the buffer";
-            }
-        }
-        const int64_t mstart = (int64_t)nb[4] + x0 - 4, n_mask = ((count + 8 + 3) / 4) * 4;
-        if (mstart % 4 || mstart < -MASK_MARGIN || mstart + n_mask > ns + MASK_MARGIN) return "link-word copy bounds";
-        for (int x = x0; x < x0 + count; ++x) {
-            const int64_t bx = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
-            if (flags[bx] == LBM_FLUID) {
-                if (seen[bx]++) return "fluid cell in two segments";
-            }
-        }
-    }
-    for (int64_t b = 0; b < (int64_t)seen.size(); ++b)
-        if ((flags[b] == LBM_FLUID) != (seen[b] == 1)) return "fluid cell not covered by exactly one segment";
-    std::fill(seen.begin(), seen.end(), 0);
+
     for (const int2 &c : ix.chunks) {
         const int r = c.x, x0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
         const uint32_t lanes = ((uint32_t)c.y >> CHUNK_LANES_SHIFT) & 0xFFu;
         if (r < 0 || r >= nrows || x0 % CHUNK) return "bad chunk";
+        for (int j = 0; j < 9; ++j)
+            if (ix.row_nb[(size_t)r * ROW_RECORD_INTS + j] % CHUNK) return "row base not chunk aligned";
         const int y = r % ix.ny_e - 1, z = r / ix.ny_e - 1;
         for (int l = 0; l < CHUNK; ++l) {
             if (!((lanes >> l) & 1u)) continue;
@@ -242,6 +206,8 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
             if (s < 0 || s >= ns) return "pull slot outside the buffer";
         }
     }
+    for (int64_t b = 0; b < (int64_t)seen.size(); ++b)
+        if ((flags[b] == LBM_FLUID) != (seen[b] == 1)) return "fluid cell not in exactly one chunk lane";
     for (const int4 &n : ix.bnodes)
         if (n.z < 0 || n.z >= ns || ix.row_nb[(size_t)n.y * ROW_RECORD_INTS + 4] + n.x != n.z) return "boundary node";
     (void)periodic;
@@ -260,7 +226,7 @@ extern "C" lbm_status lbm_check_layout(const uint8_t *flags, int32_t nx, int32_t
     if (out) {
         out[0] = ix.n_active;
         out[1] = ix.nslots;
-        out[2] = (int64_t)(ix.segs.size() / lbm::SEG_RECORD_INT4);
+        out[2] = (int64_t)ix.row_nb.size() / lbm::ROW_RECORD_INTS;
         out[3] = (int64_t)ix.chunks.size();
         out[4] = (int64_t)ix.bnodes.size();
         out[5] = ix.n_ghost;

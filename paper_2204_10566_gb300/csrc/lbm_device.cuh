@@ -29,11 +29,12 @@
 
 #include "lbm_internal.h"
 
-// Minimum resident blocks per SM requested for the step kernel (caps its
-// registers: 65536 / (256 * blocks)).
+// Minimum resident blocks per SM requested for the FP32 / FP16S step kernel
+// (caps its registers: 65536 / (threads * blocks)); FP64 is left uncapped.
 #ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 3
+#define LBM_STEP_MIN_BLOCKS 6
 #endif
+
 
 namespace lbm {
 
@@ -47,7 +48,9 @@ struct Storage<0> {  // FP64 deviations
     using T = double;
     using R = double;
     static __device__ __forceinline__ R load(const T *p, R) { return __ldg(p); }
-    static __device__ __forceinline__ R load_shared(const T *p, R) { return *p; }
+    static __device__ __forceinline__ R load_raw(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void store_raw(T *p, R v) { *p = v; }
+    static constexpr bool SCALED = false;
     static __device__ __forceinline__ void store(T *p, R v, R) { *p = v; }
 };
 
@@ -56,7 +59,9 @@ struct Storage<1> {  // FP32 deviations
     using T = float;
     using R = float;
     static __device__ __forceinline__ R load(const T *p, R) { return __ldg(p); }
-    static __device__ __forceinline__ R load_shared(const T *p, R) { return *p; }
+    static __device__ __forceinline__ R load_raw(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void store_raw(T *p, R v) { *p = v; }
+    static constexpr bool SCALED = false;
     static __device__ __forceinline__ void store(T *p, R v, R) { *p = v; }
 };
 
@@ -65,7 +70,9 @@ struct Storage<2> {  // FP16 (f - w) * s, FP32 arithmetic
     using T = __half;
     using R = float;
     static __device__ __forceinline__ R load(const T *p, R inv_s) { return __half2float(__ldg(p)) * inv_s; }
-    static __device__ __forceinline__ R load_shared(const T *p, R inv_s) { return __half2float(*p) * inv_s; }
+    static __device__ __forceinline__ R load_raw(const T *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void store_raw(T *p, R v) { *p = __float2half_rn(v); }
+    static constexpr bool SCALED = true;
     static __device__ __forceinline__ void store(T *p, R v, R s) { *p = __float2half_rn(v * s); }
 };
 
@@ -157,9 +164,13 @@ __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Collision with the default ghost rates (all 1).  d holds f_i - w_i on entry
-// and f*_i - w_i on exit; rho, u receive the (conserved) moments.
-template <class R>
-__device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &ux, R &uy, R &uz) {
+// and f*_i - w_i on exit; rho, u receive the (conserved) moments.  With
+// SCALED, d holds (f_i - w_i) / in_scale on entry and (f*_i - w_i) * out_scale
+// on exit: the scale is applied to the ten moments and to the eight output
+// coefficients instead of to the 54 populations.
+template <class R, bool SCALED = false>
+__device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &ux, R &uy, R &uz,
+                                               R in_scale = R(1), R out_scale = R(1)) {
     // x-pass of the moment cascade: per (cy, cz) line, sums weighted by 1, cx, cx^2.
     R s0[9], s1[9], s2[9];
 #pragma unroll
@@ -188,6 +199,18 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
         }
         if (cy != 0 && cz != 0) pyz += (cy * cz) > 0 ? s0[j] : -s0[j];
     }
+    if constexpr (SCALED) {
+        drho *= in_scale;
+        jx *= in_scale;
+        jy *= in_scale;
+        jz *= in_scale;
+        pxx *= in_scale;
+        pyy *= in_scale;
+        pzz *= in_scale;
+        pxy *= in_scale;
+        pxz *= in_scale;
+        pyz *= in_scale;
+    }
     rho = R(1) + drho;
     const R inv = recip(rho);
     ux = jx * inv;
@@ -196,7 +219,8 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
     // Second-order central Hermite moments sum_i ((c-u)_a (c-u)_b - theta0 delta_ab) f_i,
     // from the deviation moments (sum c_a c_b w = theta0 delta_ab).
     const R th = theta0<R>();
-    const R k = R(1) - omega;
+    const R k = SCALED ? (R(1) - omega) * out_scale : R(1) - omega;
+    const R rho_o = SCALED ? rho * out_scale : rho, drho_o = SCALED ? drho * out_scale : drho;
     const R Axx = k * (pxx - rho * ux * ux - th * drho);
     const R Ayy = k * (pyy - rho * uy * uy - th * drho);
     const R Azz = k * (pzz - rho * uz * uz - th * drho);
@@ -221,8 +245,8 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
         const R C0 = Ayy * g2<R>(cy) * gz0 + Azz * gy0 * g2<R>(cz) + Ayz * gy1 * gz1;
         const R B1 = Axy * gy1 * gz0 + Axz * gy0 * gz1;
         const R B2 = Axx * E;
-        const R Bw = drho * (wy * w1<R>(cz)) + rho * D + C0;
-        const R Bd = rho * E + C0;
+        const R Bw = drho_o * (wy * w1<R>(cz)) + rho_o * D + C0;
+        const R Bd = rho_o * E + C0;
         // cx = 0: w = 2/3, d = -ux^2, g1 = -2 ux, g2 = -1
         d[3 * j + 1] = R(2) / R(3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
         // cx = +-1: w = 1/6, d = (ux^2 +- ux)/2, g1 = ux +- 1/2, g2 = 1/2
@@ -356,7 +380,7 @@ elem(int i, int64_t stride, int s) {
 // from slot nb[j] + x - cx of population array i.  For a wall link that slot
 // is the ghost slot holding f*_{26-i}(x) (halfway bounce-back, i.e.
 // Bouzidi's interpolated bounce-back at q = 1/2, Sec. 2.2).
-template <int P, bool WIDE>
+template <int P, bool WIDE, bool RAW = false>
 __device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], int x, typename Storage<P>::R (&d)[27]) {
     using S = Storage<P>;
     using T = typename S::T;
@@ -364,7 +388,10 @@ __device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], in
     const T *fin = static_cast<const T *>(a.fin);
     const R inv_s = R(a.inv_scale);
 #pragma unroll
-    for (int i = 0; i < 27; ++i) d[i] = S::load(fin + elem<WIDE>(i, a.stride, nb[i / 3] + x - cx_of(i)), inv_s);
+    for (int i = 0; i < 27; ++i) {
+        const T *p = fin + elem<WIDE>(i, a.stride, nb[i / 3] + x - cx_of(i));
+        d[i] = RAW ? S::load_raw(p) : S::load(p, inv_s);  // RAW: storage value, scale applied later
+    }
 }
 
 // ------------------------------------------------------------------- inlet
@@ -448,12 +475,21 @@ __device__ __forceinline__ void collide(typename Storage<P>::R (&d)[27], const F
 
 // Post-collision state of one cell is in d; write it to its own slot, the
 // ghost slots of its wall links, and (periodic x) its wrap-around copies.
-template <int P, bool WIDE>
+template <int P, bool WIDE, bool RAW = false>
 __device__ __forceinline__ void store_cell_state(const StepArgs &a, const int (&nb)[9], int x, int slot, uint32_t links,
                                                  const typename Storage<P>::R (&d)[27]) {
-    using S = Storage<P>;
-    using T = typename S::T;
-    using R = typename S::R;
+    using S0 = Storage<P>;
+    using T = typename S0::T;
+    using R = typename S0::R;
+    // RAW: d already holds storage values (scale applied by the collision)
+    struct S {
+        static __device__ __forceinline__ void store(T *p, R v, R sc) {
+            if constexpr (RAW)
+                S0::store_raw(p, v);
+            else
+                S0::store(p, v, sc);
+        }
+    };
     const R s = R(a.scale);
     T *fout = static_cast<T *>(a.fout);
 #pragma unroll
@@ -494,7 +530,7 @@ __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, 
 // One time step of every fluid cell (Sec. 2.1 evolution equation, pull
 // form): gather, collide, store, refill the ghost slots of its wall links.
 template <int P, bool GHOST1, bool WIDE>
-__global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
     using R = typename Storage<P>::R;
     const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
     const int chunk = gt / CHUNK;
@@ -511,9 +547,13 @@ __global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step(cons
             const uint32_t links = __ldg(a.mask + slot) & LINK_MASK;  // needed after the collision only
             R d[27];
             R rho, ux, uy, uz;
-            gather<P, WIDE>(a, nb, x, d);
-            collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
-            store_cell_state<P, WIDE>(a, nb, x, slot, links, d);
+            constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
+            gather<P, WIDE, RAW>(a, nb, x, d);
+            if constexpr (RAW)
+                collide_ghost1<R, true>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale), R(a.scale));
+            else
+                collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
+            store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
             record_cell(a, slot, rho, ux, uy, uz, hv);
         }
     }
@@ -577,221 +617,6 @@ __global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
         record_cell(a, slot, rho, ux, uy, uz, hv);
     }
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials + (size_t)a.fluid_blocks * REDUCE_SLOTS);
-}
-
-// ------------------------------------------- staged (bulk-copy) step kernel
-
-// PTX wrappers: mbarrier (shared::cta) and 1-D bulk async copy global -> shared.
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for phase `parity` of a barrier for at most limit_ns; false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // 1 s
-constexpr uint32_t STATUS_TIMEOUT = 2u;
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-template <int P>
-struct Staging {
-    using T = typename Storage<P>::T;
-    static constexpr int HALO = 16 / (int)sizeof(T);  // elements of 16 bytes: copy alignment
-    static constexpr int W = SEGMENT + 2 * HALO;       // staged row width (elements)
-    static constexpr int MW = SEGMENT + 8;             // staged link words
-    static constexpr size_t POP_BYTES = (size_t)27 * W * sizeof(T);
-    static constexpr size_t BUF_BYTES = (POP_BYTES + (size_t)MW * 4 + 127) & ~(size_t)127;
-    static constexpr size_t SMEM_BYTES = STAGES * BUF_BYTES;
-};
-
-// Segment header staged with each buffer: row, x0, count, nb[9].
-struct SegInfo {
-    int row, x0, count, pad;
-    int nb[9];
-    int pad2[3];
-};
-
-// One time step of every fluid cell, staged and warp-specialised.  Each
-// block walks segments (runs of up to SEGMENT cells of one row).  Its
-// producer warp stages, per segment, the 27 pull rows (population i comes
-// from row j(i) at x - cx, x in [x0 - 1, x0 + count]) and the link words into
-// a ring of STAGES shared-memory buffers with bulk async copies, completing
-// on the buffer's "full" mbarrier; the consumer warps (one thread per cell)
-// wait on "full", collide from shared memory at compile-time offsets, store
-// to global memory, and release the buffer on its "empty" mbarrier.  Every
-// wait is bounded (WAIT_LIMIT_NS); on expiry the kernel raises
-// STATUS_TIMEOUT, lets its own copies land, and returns.
-template <int P, bool GHOST1, bool WIDE>
-__global__ void __launch_bounds__(STAGED_THREADS) k_step_staged(const StepArgs a) {
-    using St = Staging<P>;
-    using S = Storage<P>;
-    using T = typename S::T;
-    using R = typename S::R;
-    constexpr int HALO = St::HALO, W = St::W;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
-    __shared__ SegInfo info[STAGES];
-    __shared__ int abort_flag;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < STAGES; ++b) {
-            mbar_init(&full[b], 1);
-            mbar_init(&empty[b], CONSUMER_WARPS);
-        }
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    if (warp == 0) {
-        // ------------------------------------------------------------ producer
-        if (lane != 0) return;
-        const T *fin = static_cast<const T *>(a.fin);
-        int seg = blockIdx.x;
-        int it = 0;
-        int4 r0 = make_int4(0, 0, 0, 0), r1 = r0, r2 = r0;
-        if (seg < a.nsegs) {
-            r0 = __ldg(a.segs + SEG_RECORD_INT4 * seg);
-            r1 = __ldg(a.segs + SEG_RECORD_INT4 * seg + 1);
-            r2 = __ldg(a.segs + SEG_RECORD_INT4 * seg + 2);
-        }
-        for (; seg < a.nsegs; seg += gridDim.x, ++it) {
-            const int b = it % STAGES;
-            const int next = seg + gridDim.x;  // prefetch the next record while this one is staged
-            int4 n0 = r0, n1 = r1, n2 = r2;
-            if (next < a.nsegs) {
-                n0 = __ldg(a.segs + SEG_RECORD_INT4 * next);
-                n1 = __ldg(a.segs + SEG_RECORD_INT4 * next + 1);
-                n2 = __ldg(a.segs + SEG_RECORD_INT4 * next + 2);
-            }
-            if (it >= STAGES && !mbar_wait_bounded(&empty[b], (uint32_t)(it / STAGES - 1) & 1u, WAIT_LIMIT_NS)) {
-                atomicOr(a.status, STATUS_TIMEOUT);
-                atomicExch(&abort_flag, 1);
-                break;
-            }
-            if (*(volatile int *)&abort_flag) break;
-            SegInfo &in = info[b];
-            const int nb[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r0.w};
-            in.row = r0.x;
-            in.x0 = r0.y;
-            in.count = r0.z;
-#pragma unroll
-            for (int j = 0; j < 9; ++j) in.nb[j] = nb[j];
-            const int n_el = ((r0.z + 2 * HALO + HALO - 1) / HALO) * HALO;  // multiple of 16 bytes
-            const int n_mask = ((r0.z + 8 + 3) / 4) * 4;
-            const uint32_t pop_bytes = (uint32_t)(n_el * (int)sizeof(T));
-            mbar_arrive_expect_tx(&full[b], 27u * pop_bytes + (uint32_t)n_mask * 4u);
-            T *dst = reinterpret_cast<T *>(smem + b * St::BUF_BYTES);
-#pragma unroll
-            for (int i = 0; i < 27; ++i)
-                bulk_copy_g2s(dst + i * W, fin + ((int64_t)i * a.stride + nb[i / 3] + r0.y - HALO), pop_bytes, &full[b]);
-            bulk_copy_g2s(smem + b * St::BUF_BYTES + St::POP_BYTES, a.mask + (nb[4] + r0.y - 4), (uint32_t)n_mask * 4u,
-                          &full[b]);
-            r0 = n0;
-            r1 = n1;
-            r2 = n2;
-        }
-        // let every copy issued by this block land before leaving
-        const int last = it < STAGES ? it : STAGES;
-        for (int k = 1; k <= last; ++k) {
-            const int u = it - k;  // use index of the buffer's last stage
-            mbar_wait_bounded(&full[u % STAGES], (uint32_t)(u / STAGES) & 1u, WAIT_LIMIT_NS);
-        }
-        return;
-    }
-
-    // --------------------------------------------------------------- consumers
-    const int t = threadIdx.x - 32;  // cell lane within the segment
-    double hv[6] = {0, 0, 0, 0, 0, 0};
-    const R inv_s = R(a.inv_scale);
-    int it = 0;
-    for (int seg = blockIdx.x; seg < a.nsegs; seg += gridDim.x, ++it) {
-        const int b = it % STAGES;
-        if (!mbar_wait_bounded(&full[b], (uint32_t)(it / STAGES) & 1u, WAIT_LIMIT_NS)) {
-            if (lane == 0) {
-                atomicOr(a.status, STATUS_TIMEOUT);
-                atomicExch(&abort_flag, 1);
-            }
-            break;
-        }
-        const SegInfo &in = info[b];
-        if (t < in.count) {
-            const uint32_t *mw = reinterpret_cast<const uint32_t *>(smem + b * St::BUF_BYTES + St::POP_BYTES);
-            const uint32_t m = mw[t + 4];
-            if (((m >> TYPE_SHIFT) & 3u) == TYPE_FLUID) {
-                const T *src = reinterpret_cast<const T *>(smem + b * St::BUF_BYTES) + t + HALO;
-                R d[27];
-#pragma unroll
-                for (int i = 0; i < 27; ++i) d[i] = S::load_shared(src + i * W - cx_of(i), inv_s);
-                int nb[9];
-#pragma unroll
-                for (int j = 0; j < 9; ++j) nb[j] = in.nb[j];
-                const int x = in.x0 + t;
-                const int slot = nb[4] + x;
-                R rho, ux, uy, uz;
-                collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
-                store_cell_state<P, WIDE>(a, nb, x, slot, m & LINK_MASK, d);
-                record_cell(a, slot, rho, ux, uy, uz, hv);
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[b]);
-        if (*(volatile int *)&abort_flag) break;
-    }
-    if (a.flags & STEP_REDUCE) {  // one partial per consumer warp, fixed order
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const double v = __shfl_down_sync(0xffffffffu, hv[k], o);
-                hv[k] = (k == 4) ? fmax(hv[k], v) : hv[k] + v;
-            }
-        if (lane == 0) {
-            double *p = a.partials + ((size_t)blockIdx.x * CONSUMER_WARPS + (warp - 1)) * REDUCE_SLOTS;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) p[k] = hv[k];
-        }
-    }
 }
 
 // ---------------------------------------------------------- utility kernels
@@ -966,57 +791,22 @@ inline int step_blocks(int32_t nchunks) {
     return (int)((threads + STEP_THREADS - 1) / STEP_THREADS);
 }
 
-#ifndef LBM_STAGED
-#define LBM_STAGED 0
-#endif
-
-template <int P, bool G, bool WD>
-int staged_grid(int device) {
-    static int per_sm[64] = {0};
-    static int sms[64] = {0};
-    if (device < 0 || device >= 64) device = 0;
-    if (per_sm[device] == 0) {
-        cudaFuncSetAttribute(k_step_staged<P, G, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Staging<P>::SMEM_BYTES);
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_staged<P, G, WD>, STAGED_THREADS,
-                                                      Staging<P>::SMEM_BYTES);
-        cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
-        per_sm[device] = n > 0 ? n : 1;
-    }
-    return per_sm[device] * sms[device];
-}
-
-// Grid of the staged kernel (persistent blocks, at most one per segment).
-template <int P>
-int staged_blocks(int32_t nsegs, int device) {
-    const int g = std::max(std::max(staged_grid<P, true, false>(device), staged_grid<P, false, false>(device)),
-                           std::max(staged_grid<P, true, true>(device), staged_grid<P, false, true>(device)));
-    return std::max(1, std::min(nsegs, g));
-}
-
 // Partial-sum slots written by the fluid kernel of one step.
 template <int P>
-int step_fluid_blocks(int32_t nchunks, int32_t nsegs, int device) {
-    if (!LBM_STAGED) return step_blocks(nchunks);
-    return staged_blocks<P>(nsegs, device) * CONSUMER_WARPS;
+int step_fluid_blocks(int32_t nchunks) {
+    return step_blocks(nchunks);
 }
 
 template <int P, bool G, bool WD>
 void launch_fluid(const StepArgs &a, cudaStream_t s) {
-    if (LBM_STAGED) {
-        const int grid = a.fluid_blocks / CONSUMER_WARPS;
-        k_step_staged<P, G, WD><<<grid, STAGED_THREADS, Staging<P>::SMEM_BYTES, s>>>(a);
-    } else {
-        k_step<P, G, WD><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
-    }
+    k_step<P, G, WD><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
 }
 
 template <int P>
 cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s) {
     const bool wide = a.stride > MAX_SLOTS_32;
     const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
-    if (a.nsegs > 0) {
+    if (a.nchunks > 0) {
         if (ghost1)
             wide ? launch_fluid<P, true, true>(a, s) : launch_fluid<P, true, false>(a, s);
         else
@@ -1089,7 +879,7 @@ cudaError_t launch_init_eq(void *f, const int32_t *soa, int64_t n, int64_t strid
 
 #define LBM_INSTANTIATE(P)                                                                                         \
     template cudaError_t launch_step<P>(const StepArgs &, bool, cudaStream_t);                                     \
-    template int step_fluid_blocks<P>(int32_t, int32_t, int);                                                       \
+    template int step_fluid_blocks<P>(int32_t);                                                                     \
     template cudaError_t launch_reduce<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \
                                           cudaStream_t);                                                           \
     template cudaError_t launch_fill_ghosts<P>(void *, const uint32_t *, const int2 *, const int4 *, int32_t,      \

@@ -16,18 +16,10 @@ namespace lbm {
 // (fixed y, z).  Every row's storage starts and ends on a CHUNK boundary so
 // that chunk lanes map to consecutive, aligned storage slots.
 constexpr int CHUNK = 8;
-constexpr int STEP_THREADS = 256;
-// Staged step kernel: a segment is a run of at most SEGMENT fluid-row cells
-// starting on a CHUNK boundary; its 27 pull rows are staged in shared memory
-// by bulk async copies.  Each block has one producer warp and
-// SEGMENT / 32 consumer warps (one thread per cell) sharing a ring of
-// STAGES staged segments.
-constexpr int SEGMENT = 64;
-constexpr int CONSUMER_WARPS = SEGMENT / 32;
-constexpr int STAGED_THREADS = 32 * (1 + CONSUMER_WARPS);
-constexpr int STAGES = 3;
-// Segment record: 3 x int4 = {row, x0, count, nb[8]}, nb[0..3], nb[4..7].
-constexpr int SEG_RECORD_INT4 = 3;
+#ifndef LBM_STEP_THREADS
+#define LBM_STEP_THREADS 128
+#endif
+constexpr int STEP_THREADS = LBM_STEP_THREADS;
 constexpr int REDUCE_SLOTS = 8;  // doubles per block partial
 
 // Per-slot link word.
@@ -84,8 +76,6 @@ struct StepArgs {
     const int4 *bnodes;     // boundary nodes (x, row, slot, link word)
     int32_t nbnodes;
     int32_t fluid_blocks;   // blocks of the fluid kernel (offset of the boundary kernel's partials)
-    const int4 *segs;       // segment records of fluid cells (SEG_RECORD_INT4 int4 each)
-    int32_t nsegs;
     uint32_t *status;       // bit 1: a bounded device wait gave up
     int32_t nx, ny, nz, ny_e;
     int32_t flags;          // STEP_REDUCE | STEP_STATS
@@ -110,7 +100,7 @@ template <int P>
 cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s);
 // Blocks of one step's fluid kernel (partial-sum slots it writes).
 template <int P>
-int step_fluid_blocks(int32_t nchunks, int32_t nsegs, int device);
+int step_fluid_blocks(int32_t nchunks);
 template <int P>
 cudaError_t launch_reduce(const void *f, const int32_t *slot_of_active, int64_t n, int64_t stride, float inv_scale,
                           double *partials, cudaStream_t s);
@@ -150,16 +140,14 @@ struct HostIndex {
     std::vector<int32_t> row_nb;          // [rows][ROW_RECORD_INTS]
     std::vector<int2> chunks;             // chunk records (fluid cells)
     std::vector<int4> bnodes;             // inlet/outlet nodes: x, row, slot, link word
-    std::vector<int4> segs;               // segment records (SEG_RECORD_INT4 int4 each)
     std::vector<uint32_t> mask;           // [nslots]
     std::vector<int32_t> slot_of_active;  // [n_active], active order = increasing box index
     std::vector<int64_t> box_of_active;   // [n_active]
 };
 
-// Margin (elements) kept readable before and after every population buffer
-// and (in link words) around the link-word array, so that the staged
-// kernel's aligned row copies never leave the allocation.
-inline int64_t buffer_margin(int nx) { return ((int64_t)nx + SEGMENT + 64 + 63) & ~(int64_t)63; }
+// Slack (elements) allocated before and after every population buffer and
+// around the link-word array (keeps 256-byte alignment of the buffers).
+inline int64_t buffer_margin(int nx) { return ((int64_t)nx + 64 + 63) & ~(int64_t)63; }
 constexpr int64_t MASK_MARGIN = 64;
 
 // Returns "" on success, else a description of the inconsistency.
