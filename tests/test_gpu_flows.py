@@ -1,0 +1,160 @@
+"""Flow-level checks of the CUDA path (GPU required): periodic Taylor-Green
+vortices against the oracle and the exact decay, and the time-averaged axial
+velocity of the transitional / turbulent nozzles across storage precisions
+(pointwise agreement is lost to chaos there; the averaged profiles must agree
+within 2 %)."""
+import numpy as np
+import pytest
+
+from paper_2204_10566_gb300 import inputs as I
+
+from gpu_util import gpu_lattice, max_rel, omega_of_nu, oracle_lattice, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BOX = 1
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2204_10566_gb300 import build
+
+    build.build()
+    from paper_2204_10566_gb300 import lbm as m
+
+    return m
+
+
+def tgv3d_fields(n, u0):
+    """3-D Taylor-Green vortex initial field on an n^3 periodic box (cell
+    centres), with the pressure of the incompressible solution."""
+    k = 2 * np.pi / n
+    c = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    u = np.stack([u0 * np.sin(k * X) * np.cos(k * Y) * np.cos(k * Z),
+                  -u0 * np.cos(k * X) * np.sin(k * Y) * np.cos(k * Z),
+                  np.zeros_like(X)], axis=-1).reshape(-1, 3)
+    p = u0 ** 2 / 16.0 * (np.cos(2 * k * X) + np.cos(2 * k * Y)) * (np.cos(2 * k * Z) + 2.0)
+    rho = (1.0 + 3.0 * p).reshape(-1)
+    return rho, u
+
+
+@pytest.fixture(scope="module")
+def tgv64_oracle(orc):
+    n, u0, Re = 64, 0.04, 400.0
+    nu = u0 * n / (2 * np.pi) / Re
+    flags = np.ones((n, n, n), dtype=np.uint8)
+    rho, u = tgv3d_fields(n, u0)
+    O = oracle_lattice(orc, flags, nu, periodic=7)
+    O.init_equilibrium(rho, u)
+    f0 = O.f.copy()
+    O.step(4)
+    return flags, nu, rho, u, f0, O
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_tgv64_against_oracle(lbm, tgv64_oracle, precision):
+    """Taylor-Green vortex at 64^3, Re 400, four steps from the same initial
+    populations: FP64 elementwise, FP32 / FP16S on the velocity."""
+    flags, nu, rho, u, f0, O = tgv64_oracle
+    G = gpu_lattice(lbm, flags, precision, nu, periodic=7)
+    G.set_populations(f0, layout=BOX)
+    G.step(4).sync()
+    if precision == "fp64":
+        assert max_rel(G.get_populations(BOX), O.f) < 1e-12
+    else:
+        _, ug = G.moments(BOX)
+        tol = 1e-5 if precision == "fp32" else 1e-3
+        assert rel_l2(ug, O.moments()[:, 1:]) < tol
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_tgv2d_decay_rate(lbm, n):
+    """2-D Taylor-Green vortex (uniform in z; an exact Navier-Stokes
+    solution): kinetic energy decays as exp(-4 nu k^2 t).  FP32 on the GPU."""
+    u0 = 0.02
+    nu = 0.01 * n / 64.0
+    k = 2 * np.pi / n
+    c = np.arange(n) + 0.5
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    ux = u0 * np.sin(k * X) * np.cos(k * Y)
+    uy = -u0 * np.cos(k * X) * np.sin(k * Y)
+    rho = 1.0 - 3.0 * u0 ** 2 / 4.0 * (np.cos(2 * k * X) + np.cos(2 * k * Y))
+    nz = 4
+    flags = np.ones((nz, n, n), dtype=np.uint8)
+    u = np.zeros((nz, n, n, 3))
+    u[..., 0] = ux
+    u[..., 1] = uy
+    G = gpu_lattice(lbm, flags, "fp32", nu, periodic=7)
+    G.init_fields(np.broadcast_to(rho, (nz, n, n)).reshape(-1), u.reshape(-1, 3), layout=BOX)
+    steps = int(0.5 / (nu * k * k))
+    G.step(steps // 4).sync()
+    e0 = (G.moments(BOX)[1] ** 2).sum()
+    G.step(steps - steps // 4).sync()
+    e1 = (G.moments(BOX)[1] ** 2).sum()
+    rate = -np.log(e1 / e0) / (4 * (steps - steps // 4)) / (nu * k * k)
+    assert abs(rate - 1.0) < 5e-3
+
+
+def nozzle_profile_run(lbm, name, precision, steps, avg_from):
+    """<u_z> time-averaged over steps avg_from+1 .. steps (FP64 accumulators):
+    centreline, eight cross-section planes, and the plane positions."""
+    w = I.WORKLOADS[name]
+    flags = I.workload_flags(name)
+    G = lbm.Lattice(flags, precision)
+    G.set_params(Re=w["Re"], u_char=w["u_throat"], L_char=float(w["d"]), u_in=I.inlet_mean_velocity(w),
+                 d_in=float(w["D"]), profile=w["profile"], noise_amp=w["noise"], noise_seed=w["seed"])
+    G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
+    G.step(avg_from)
+    G.stats_begin(1)
+    G.step(steps - avg_from).sync()
+    m1, m2, n = G.stats_get(BOX)
+    G.close()
+    nz, ny, nx = flags.shape
+    m1 = m1.reshape(nz, ny, nx)
+    zs = np.linspace(0, nz - 1, 10).astype(int)[1:-1]
+    return m1[:, ny // 2, nx // 2], m1[zs], zs, n
+
+
+def expansion_start(name):
+    w = I.WORKLOADS[name]
+    return w["D"] + I.cone_length(w["D"], w["d"]) + 4 * w["d"]
+
+
+def check_statistics(name, ref, run, tol=0.02):
+    """Averages are compared where they are statistically converged within
+    the run: profiles up to the sudden expansion (inlet pipe, cone, throat),
+    where the jet has not yet broken down, and the plane-integrated axial
+    flux (fixed by mean mass conservation) on every plane.  Downstream of
+    the expansion the flow is chaotic and 10 000 steps are less than one
+    flow-through time, so pointwise averages differ between any two runs."""
+    rc, rp, zs, _ = ref
+    c, p, _, _ = run
+    z_exp = expansion_start(name)
+    assert rel_l2(c[:z_exp], rc[:z_exp]) < tol
+    up = zs < z_exp
+    assert rel_l2(p[up], rp[up]) < tol
+    flux_ref = rp.reshape(len(zs), -1).sum(1)
+    flux = p.reshape(len(zs), -1).sum(1)
+    assert np.max(np.abs(flux - flux_ref) / np.abs(flux_ref)) < tol
+
+
+def test_transitional_nozzle_time_averaged_profiles(lbm):
+    """Re 3500 nozzle (96x96x800, parabolic inlet + 1 % noise), 20 000 steps
+    averaged over steps 10 001-20 000: FP32 and FP16-shifted <u_z> within 2 %
+    of the FP64 GPU run."""
+    name = "nozzle_re3500_96x96x800"
+    ref = nozzle_profile_run(lbm, name, "fp64", 20000, 10000)
+    assert ref[3] == 10000
+    for precision in ("fp32", "fp16s"):
+        check_statistics(name, ref, nozzle_profile_run(lbm, name, precision, 20000, 10000))
+
+
+def test_turbulent_nozzle_fp16s_vs_fp32(lbm):
+    """Re 6500 nozzle (144x144x1200, parabolic inlet + 2 % noise): FP16-shifted
+    storage against FP32, FP64 statistics accumulators, 20 000 steps averaged
+    over the second half: <u_z> within 2 %."""
+    name = "nozzle_re6500_144x144x1200"
+    ref = nozzle_profile_run(lbm, name, "fp32", 20000, 10000)
+    check_statistics(name, ref, nozzle_profile_run(lbm, name, "fp16s", 20000, 10000))
