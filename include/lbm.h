@@ -270,6 +270,79 @@ lbm_status lbm_totals_noalloc(const void *f, int32_t precision, float fp16_scale
  * row padding), bytes of one population buffer, device bytes held. */
 lbm_status lbm_layout_info(lbm_ctx *ctx, int64_t *slots, int64_t *buffer_bytes, int64_t *device_bytes);
 
+/* ------------------------------------------------------------------ serving
+ * A request server runs many lattices (nozzle / pipe runs of different
+ * sizes, Re, step counts and storage precisions) on one GPU with continuous
+ * batching: queued requests are admitted into resident slots as memory and
+ * slots free up (admission by exact device footprint against a budget),
+ * and every scheduling tick advances all resident lattices together with one
+ * persistent multi-lattice launch per precision and step, replayed from a
+ * captured CUDA graph.  Finished lattices are read back (rho, u) and freed.
+ * Each lattice is advanced by exactly the arithmetic of lbm_step, so a
+ * result does not depend on what else is resident.  (This is a service
+ * around the method of the paper, which has no counterpart.) */
+
+#define LBM_SERVER_MAX_SLOTS 64
+
+typedef struct lbm_server lbm_server;
+
+typedef struct {
+    int32_t device;
+    void *stream;            /* cudaStream_t (NULL: default stream) */
+    lbm_allocator allocator; /* alloc == NULL: cudaMalloc / cudaFree */
+    int64_t budget_bytes;    /* device bytes the resident lattices may hold (> 0) */
+    int32_t max_slots;       /* resident lattices at most, 1..LBM_SERVER_MAX_SLOTS */
+    int32_t steps_per_tick;  /* lattice steps per tick, even, 2..1024 */
+} lbm_server_desc;
+
+typedef struct {
+    int32_t nx, ny, nz, periodic;
+    int32_t precision;       /* LBM_FP32 or LBM_FP16S */
+    float fp16_scale;        /* 0 selects 4096 */
+    const uint8_t *flags;    /* host flag field [nz][ny][nx], copied by lbm_server_submit */
+    lbm_params params;       /* default ghost rates only */
+    int64_t steps;           /* time steps to run, >= 1; the lattice starts at rest (rho 1, u 0) */
+} lbm_request;
+
+enum { LBM_REQ_QUEUED = 0, LBM_REQ_RUNNING = 1, LBM_REQ_DONE = 2, LBM_REQ_CANCELLED = 3, LBM_REQ_FAILED = 4 };
+
+/* Create / destroy a server.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+lbm_status lbm_server_create(const lbm_server_desc *desc, lbm_server **out);
+lbm_status lbm_server_destroy(lbm_server *s);
+const char *lbm_server_last_error(const lbm_server *s);
+
+/* Queue a request; *id receives its handle.  The flag field is checked and
+ * its sparse index built in a background host thread.  Errors: LBM_ERR_ARG
+ * (bad request), LBM_ERR_OOM (its lattice can never fit the budget). */
+lbm_status lbm_server_submit(lbm_server *s, const lbm_request *req, int64_t *id);
+
+/* One scheduling tick: admit queued requests whose index is built (in
+ * submission order, while a slot is free and the footprint fits), advance
+ * every resident lattice by up to steps_per_tick steps, retire the finished
+ * ones (read back rho, u; free their memory).  Blocks until the tick's work
+ * is done.  Outputs (may be NULL): resident lattices, queued requests. */
+lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued);
+
+/* State (LBM_REQ_*) and steps done of a request. */
+lbm_status lbm_server_poll(lbm_server *s, int64_t id, int32_t *state, int64_t *steps_done);
+
+/* Number of active cells of a request (known once its index is built;
+ * LBM_ERR_STATE before). */
+lbm_status lbm_server_cells(lbm_server *s, int64_t id, int64_t *active_cells);
+
+/* Final density rho[n] and velocity u[n][3] of a finished request, in the
+ * active order of its flag field; releases the stored result.
+ * Errors: LBM_ERR_STATE if not finished. */
+lbm_status lbm_server_result(lbm_server *s, int64_t id, double *rho, double *u);
+
+/* Cancel a queued or running request (its memory is freed at the next tick). */
+lbm_status lbm_server_cancel(lbm_server *s, int64_t id);
+
+/* Counters: out[0] cell updates done, out[1] ticks, out[2] device bytes held
+ * now, out[3] peak device bytes, out[4] graph launches, out[5] graph
+ * captures, out[6] requests finished, out[7] requests queued. */
+lbm_status lbm_server_info(lbm_server *s, double out[8]);
+
 #ifdef __cplusplus
 }
 #endif

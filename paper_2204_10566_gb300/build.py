@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
-SOURCES = ["api.cu", "common.cu", "geometry.cpp", "step_fp64.cu", "step_fp32.cu", "step_fp16s.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "common.cu", "geometry.cpp", "step_fp64.cu", "step_fp32.cu", "step_fp16s.cu", "noalloc.cu", "server.cu"]
 
 
 def nvcc():

@@ -181,6 +181,70 @@ lbm_status reset_state(lbm_ctx *c) {
 
 }  // namespace
 
+namespace lbm {
+
+// Everything a step kernel needs from a context; fin/fout/t_new describe
+// the next step from the current state, flags are cleared.
+void ctx_step_args(lbm_ctx *c, StepArgs *out) {
+    StepArgs a{};
+    a.mask = c->d_mask;
+    a.row_nb = c->d_row_nb;
+    a.chunks = c->d_chunks;
+    a.stride = c->idx.nslots;
+    a.nchunks = (int32_t)c->idx.chunks.size();
+    a.bnodes = c->d_bnodes;
+    a.nbnodes = (int32_t)c->idx.bnodes.size();
+    a.fluid_blocks = c->fluid_blocks;
+    a.status = c->d_status;
+    a.nx = c->desc.nx;
+    a.ny = c->desc.ny;
+    a.nz = c->desc.nz;
+    a.ny_e = c->idx.ny_e;
+    a.periodic_x = (c->desc.periodic & LBM_PERIODIC_X) ? 1 : 0;
+    a.profile = c->params.inlet_profile;
+    const double gr[4] = {c->params.omega3, c->params.omega4, c->params.omega5, c->params.omega6};
+    a.pd.omega = c->omega;
+    for (int q = 0; q < 4; ++q) a.pd.ghost[q] = gr[q];
+    a.pd.u_in = c->params.u_in;
+    a.pd.d_in = c->params.d_in;
+    a.pd.axis_x = c->params.axis_x;
+    a.pd.axis_y = c->params.axis_y;
+    a.pd.noise_amp = c->params.noise_amp;
+    a.pd.rho_out = c->params.rho_out;
+    a.pf.omega = (float)a.pd.omega;
+    for (int q = 0; q < 4; ++q) a.pf.ghost[q] = (float)gr[q];
+    a.pf.u_in = (float)a.pd.u_in;
+    a.pf.d_in = (float)a.pd.d_in;
+    a.pf.axis_x = (float)a.pd.axis_x;
+    a.pf.axis_y = (float)a.pd.axis_y;
+    a.pf.noise_amp = (float)a.pd.noise_amp;
+    a.pf.rho_out = (float)a.pd.rho_out;
+    a.seed = c->params.noise_seed;
+    a.scale = fp16_scale(c);
+    a.inv_scale = 1.0f / a.scale;
+    a.stats = c->d_stats;
+    a.partials = c->d_partials;
+    a.fin = c->f[c->cur];
+    a.fout = c->f[1 - c->cur];
+    a.t_new = c->t + 1;
+    a.flags = 0;
+    *out = a;
+}
+
+void ctx_advance(lbm_ctx *c, int64_t steps) {
+    c->t += steps;
+    if (steps & 1) c->cur = 1 - c->cur;
+}
+
+int64_t ctx_steps(const lbm_ctx *c) { return c->t; }
+int64_t ctx_device_bytes(const lbm_ctx *c) { return c->device_bytes; }
+bool ctx_ready(const lbm_ctx *c) { return c->has_geom && c->has_params && c->has_state; }
+bool ctx_ghost1(const lbm_ctx *c) { return c->ghost1; }
+int ctx_precision(const lbm_ctx *c) { return c->desc.precision; }
+int64_t ctx_slots(const lbm_ctx *c) { return c->idx.nslots; }
+
+}  // namespace lbm
+
 extern "C" {
 
 const char *lbm_status_string(lbm_status s) {
@@ -246,10 +310,27 @@ const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : "null
 lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     if (!c) return LBM_ERR_ARG;
     if (!flags) return fail(c, LBM_ERR_ARG, "flags is NULL");
-    DeviceGuard g(c->desc.device);
     HostIndex idx;
     std::string msg = build_index(flags, c->desc.nx, c->desc.ny, c->desc.nz, c->desc.periodic, idx);
     if (!msg.empty()) return fail(c, LBM_ERR_ARG, msg);
+    return lbm::ctx_install_index(c, std::move(idx));
+}
+
+}  // extern "C"
+
+namespace lbm {
+
+int64_t ctx_footprint(const lbm_desc &d, const HostIndex &ix) {
+    const int S = storage_bytes(d.precision);
+    const int64_t pop = 27 * ix.nslots * S + 2 * buffer_margin(d.nx) * S;
+    const int64_t blocks = std::max<int64_t>(fluid_blocks((int32_t)ix.chunks.size()) + node_blocks((int64_t)ix.bnodes.size()),
+                                             node_blocks(ix.n_active));
+    return 2 * pop + (ix.nslots + 2 * MASK_MARGIN) * 4 + (int64_t)ix.row_nb.size() * 4 + (int64_t)ix.chunks.size() * 8 +
+           (int64_t)ix.bnodes.size() * 16 + ix.n_active * 4 + blocks * REDUCE_SLOTS * 8 + 64 + 256;
+}
+
+lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
+    DeviceGuard g(c->desc.device);
     CK(cudaStreamSynchronize(c->stream), "sync before geometry change");
     release_geometry(c);
     c->idx = std::move(idx);
@@ -302,6 +383,10 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     c->t = 0;
     return LBM_OK;
 }
+
+}  // namespace lbm
+
+extern "C" {
 
 lbm_status lbm_fluid_count(lbm_ctx *c, int64_t *n) {
     lbm_status st = need(c, true, false, false);
@@ -455,43 +540,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
     if (n < 0) return fail(c, LBM_ERR_ARG, "negative step count");
     DeviceGuard g(c->desc.device);
     StepArgs a{};
-    a.mask = c->d_mask;
-    a.row_nb = c->d_row_nb;
-    a.chunks = c->d_chunks;
-    a.stride = c->idx.nslots;
-    a.nchunks = (int32_t)c->idx.chunks.size();
-    a.bnodes = c->d_bnodes;
-    a.nbnodes = (int32_t)c->idx.bnodes.size();
-    a.fluid_blocks = c->fluid_blocks;
-    a.status = c->d_status;
-    a.nx = c->desc.nx;
-    a.ny = c->desc.ny;
-    a.nz = c->desc.nz;
-    a.ny_e = c->idx.ny_e;
-    a.periodic_x = (c->desc.periodic & LBM_PERIODIC_X) ? 1 : 0;
-    a.profile = c->params.inlet_profile;
-    const double gr[4] = {c->params.omega3, c->params.omega4, c->params.omega5, c->params.omega6};
-    a.pd.omega = c->omega;
-    for (int q = 0; q < 4; ++q) a.pd.ghost[q] = gr[q];
-    a.pd.u_in = c->params.u_in;
-    a.pd.d_in = c->params.d_in;
-    a.pd.axis_x = c->params.axis_x;
-    a.pd.axis_y = c->params.axis_y;
-    a.pd.noise_amp = c->params.noise_amp;
-    a.pd.rho_out = c->params.rho_out;
-    a.pf.omega = (float)a.pd.omega;
-    for (int q = 0; q < 4; ++q) a.pf.ghost[q] = (float)gr[q];
-    a.pf.u_in = (float)a.pd.u_in;
-    a.pf.d_in = (float)a.pd.d_in;
-    a.pf.axis_x = (float)a.pd.axis_x;
-    a.pf.axis_y = (float)a.pd.axis_y;
-    a.pf.noise_amp = (float)a.pd.noise_amp;
-    a.pf.rho_out = (float)a.pd.rho_out;
-    a.seed = c->params.noise_seed;
-    a.scale = fp16_scale(c);
-    a.inv_scale = 1.0f / a.scale;
-    a.stats = c->d_stats;
-    a.partials = c->d_partials;
+    lbm::ctx_step_args(c, &a);
     for (int64_t k = 0; k < n; ++k) {
         const int64_t t_new = c->t + 1;
         a.fin = c->f[c->cur];

@@ -527,95 +527,102 @@ __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, 
     if (a.flags & STEP_REDUCE) health_values(rho, ux, uy, uz, hv);
 }
 
-// One time step of every fluid cell (Sec. 2.1 evolution equation, pull
-// form): gather, collide, store, refill the ghost slots of its wall links.
+// Update of the fluid cell in lane `lane` of chunk `chunk` (Sec. 2.1
+// evolution equation, pull form): gather, collide, store, refill the ghost
+// slots of its wall links.
 template <int P, bool GHOST1, bool WIDE>
-__global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
+__device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lane, double (&hv)[6]) {
     using R = typename Storage<P>::R;
-    const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
-    const int chunk = gt / CHUNK;
-    double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (chunk < a.nchunks) {
-        const int2 ch = __ldg(a.chunks + chunk);
-        const uint32_t cw = (uint32_t)ch.y;
-        const int lane = gt % CHUNK;
-        if ((cw >> (CHUNK_LANES_SHIFT + lane)) & 1u) {
-            const int x = (int)(cw & CHUNK_X0_MASK) + lane;
-            int nb[9];
-            load_row(a.row_nb, ch.x, nb);
-            const int slot = nb[4] + x;
-            const uint32_t links = __ldg(a.mask + slot) & LINK_MASK;  // needed after the collision only
-            R d[27];
-            R rho, ux, uy, uz;
-            constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
-            gather<P, WIDE, RAW>(a, nb, x, d);
-            if constexpr (RAW)
-                collide_ghost1<R, true>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale), R(a.scale));
-            else
-                collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
-            store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
-            record_cell(a, slot, rho, ux, uy, uz, hv);
-        }
-    }
-    if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
+    const int2 ch = __ldg(a.chunks + chunk);
+    const uint32_t cw = (uint32_t)ch.y;
+    if (!((cw >> (CHUNK_LANES_SHIFT + lane)) & 1u)) return;
+    const int x = (int)(cw & CHUNK_X0_MASK) + lane;
+    int nb[9];
+    load_row(a.row_nb, ch.x, nb);
+    const int slot = nb[4] + x;
+    const uint32_t links = __ldg(a.mask + slot) & LINK_MASK;  // needed after the collision only
+    R d[27];
+    R rho, ux, uy, uz;
+    constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
+    gather<P, WIDE, RAW>(a, nb, x, d);
+    if constexpr (RAW)
+        collide_ghost1<R, true>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale), R(a.scale));
+    else
+        collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
+    store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
+    record_cell(a, slot, rho, ux, uy, uz, hv);
 }
 
-// One time step of every inlet/outlet node: non-equilibrium extrapolation
-// (Sec. 2.2) from the interior partner x_f, whose update is recomputed here
-// from the same input state (so this kernel and k_step are independent):
+// Update of inlet/outlet node k: non-equilibrium extrapolation (Sec. 2.2)
+// from the interior partner x_f, whose update is recomputed here from the
+// same input state (so boundary and fluid updates are independent):
 //   f*_i(x_b) = f^eq_i(rho_b, u_b) + f*_i(x_f) - f^eq_i(rho_f, u_f),
 // inlet: rho_b = rho_f, u_b prescribed; outlet: rho_b = rho_out, u_b = u_f.
 template <int P, bool GHOST1, bool WIDE>
-__global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
+__device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (&hv)[6]) {
     using R = typename Storage<P>::R;
+    const int4 node = __ldg(a.bnodes + k);
+    const int x = node.x, row = node.y, slot = node.z;
+    const uint32_t m = (uint32_t)node.w;
+    const uint32_t type = (m >> TYPE_SHIFT) & 3u;
+    const FlowParams<R> &fp = flow<R>(a);
+    const int y = row % a.ny_e - 1, z = row / a.ny_e - 1;
+    const int dir = (int)(m >> DIR_SHIFT);
+    const int nx_ = (dir == 0) - (dir == 1), ny_ = (dir == 2) - (dir == 3), nz_ = (dir == 4) - (dir == 5);
+    const int xf = wrap(x + nx_, a.nx), yf = wrap(y + ny_, a.ny), zf = wrap(z + nz_, a.nz);
+    int nbf[9];
+    load_row(a.row_nb, (yf + 1) + a.ny_e * (zf + 1), nbf);
+    R d[27];
+    R rf, uxf, uyf, uzf, rho, ux, uy, uz;
+    gather<P, WIDE>(a, nbf, xf, d);
+    collide<P, GHOST1>(d, fp, rf, uxf, uyf, uzf);
+    if (type == TYPE_INLET) {
+        R speed = fp.u_in;
+        if (a.profile == LBM_PROFILE_PARABOLIC) {
+            const R rx = R(x) + R(0.5) - fp.axis_x, ry = R(y) + R(0.5) - fp.axis_y;
+            const R r2 = rx * rx + ry * ry;
+            speed = R(2) * fp.u_in * (R(1) - R(4) * r2 / (fp.d_in * fp.d_in));
+        }
+        rho = rf;
+        ux = speed * R(nx_);
+        uy = speed * R(ny_);
+        uz = speed * R(nz_);
+        if (fp.noise_amp != R(0)) {
+            const int64_t node_id = (int64_t)x + (int64_t)a.nx * ((int64_t)y + (int64_t)a.ny * z);
+            const R amp = fp.noise_amp * fp.u_in;
+            ux += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 0);
+            uy += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 1);
+            uz += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 2);
+        }
+    } else {
+        rho = fp.rho_out;
+        ux = uxf;
+        uy = uyf;
+        uz = uzf;
+    }
+    add_eq_difference<R>(rho, ux, uy, uz, rf, uxf, uyf, uzf, d);
+    int nb[9];
+    load_row(a.row_nb, row, nb);
+    store_cell_state<P, WIDE>(a, nb, x, slot, 0u, d);
+    record_cell(a, slot, rho, ux, uy, uz, hv);
+}
+
+// One time step of every fluid cell of one lattice.
+template <int P, bool GHOST1, bool WIDE>
+__global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
+    const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
+    const int chunk = gt / CHUNK;
+    double hv[6] = {0, 0, 0, 0, 0, 0};
+    if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE>(a, chunk, gt % CHUNK, hv);
+    if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
+}
+
+// One time step of every inlet/outlet node of one lattice.
+template <int P, bool GHOST1, bool WIDE>
+__global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
     const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (k < a.nbnodes) {
-        const int4 node = __ldg(a.bnodes + k);
-        const int x = node.x, row = node.y, slot = node.z;
-        const uint32_t m = (uint32_t)node.w;
-        const uint32_t type = (m >> TYPE_SHIFT) & 3u;
-        const FlowParams<R> &fp = flow<R>(a);
-        const int y = row % a.ny_e - 1, z = row / a.ny_e - 1;
-        const int dir = (int)(m >> DIR_SHIFT);
-        const int nx_ = (dir == 0) - (dir == 1), ny_ = (dir == 2) - (dir == 3), nz_ = (dir == 4) - (dir == 5);
-        const int xf = wrap(x + nx_, a.nx), yf = wrap(y + ny_, a.ny), zf = wrap(z + nz_, a.nz);
-        int nbf[9];
-        load_row(a.row_nb, (yf + 1) + a.ny_e * (zf + 1), nbf);
-        R d[27];
-        R rf, uxf, uyf, uzf, rho, ux, uy, uz;
-        gather<P, WIDE>(a, nbf, xf, d);
-        collide<P, GHOST1>(d, fp, rf, uxf, uyf, uzf);
-        if (type == TYPE_INLET) {
-            R speed = fp.u_in;
-            if (a.profile == LBM_PROFILE_PARABOLIC) {
-                const R rx = R(x) + R(0.5) - fp.axis_x, ry = R(y) + R(0.5) - fp.axis_y;
-                const R r2 = rx * rx + ry * ry;
-                speed = R(2) * fp.u_in * (R(1) - R(4) * r2 / (fp.d_in * fp.d_in));
-            }
-            rho = rf;
-            ux = speed * R(nx_);
-            uy = speed * R(ny_);
-            uz = speed * R(nz_);
-            if (fp.noise_amp != R(0)) {
-                const int64_t node_id = (int64_t)x + (int64_t)a.nx * ((int64_t)y + (int64_t)a.ny * z);
-                const R amp = fp.noise_amp * fp.u_in;
-                ux += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 0);
-                uy += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 1);
-                uz += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 2);
-            }
-        } else {
-            rho = fp.rho_out;
-            ux = uxf;
-            uy = uyf;
-            uz = uzf;
-        }
-        add_eq_difference<R>(rho, ux, uy, uz, rf, uxf, uyf, uzf, d);
-        int nb[9];
-        load_row(a.row_nb, row, nb);
-        store_cell_state<P, WIDE>(a, nb, x, slot, 0u, d);
-        record_cell(a, slot, rho, ux, uy, uz, hv);
-    }
+    if (k < a.nbnodes) boundary_node<P, GHOST1, WIDE>(a, k, hv);
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials + (size_t)a.fluid_blocks * REDUCE_SLOTS);
 }
 

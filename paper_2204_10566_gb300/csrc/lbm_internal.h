@@ -66,7 +66,7 @@ struct FlowParams {
     R u_in, d_in, axis_x, axis_y, noise_amp, rho_out;
 };
 
-struct StepArgs {
+struct alignas(16) StepArgs {
     const void *fin;        // population arrays [27][stride], storage type of the kernel
     void *fout;
     const uint32_t *mask;
@@ -154,5 +154,17 @@ constexpr int64_t MASK_MARGIN = 64;
 std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out);
 // Independent check of the index invariants the kernels rely on ("" if all hold).
 std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, int ny, int nz, int periodic);
+
+// Hooks into a context for the request server (implemented in api.cu).
+int64_t ctx_footprint(const lbm_desc &desc, const HostIndex &ix);  // device bytes lbm_set_geometry allocates
+lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx);        // allocate + upload a built index
+void ctx_step_args(lbm_ctx *c, StepArgs *out);                      // arguments of the next step
+void ctx_advance(lbm_ctx *c, int64_t steps);                        // account for steps run elsewhere
+int64_t ctx_steps(const lbm_ctx *c);
+int64_t ctx_device_bytes(const lbm_ctx *c);
+bool ctx_ready(const lbm_ctx *c);
+bool ctx_ghost1(const lbm_ctx *c);
+int ctx_precision(const lbm_ctx *c);
+int64_t ctx_slots(const lbm_ctx *c);
 
 }  // namespace lbm

@@ -56,6 +56,24 @@ class lbm_params(C.Structure):
     ]
 
 
+class lbm_server_desc(C.Structure):
+    _fields_ = [
+        ("device", C.c_int32), ("stream", C.c_void_p), ("allocator", lbm_allocator),
+        ("budget_bytes", C.c_int64), ("max_slots", C.c_int32), ("steps_per_tick", C.c_int32),
+    ]
+
+
+class lbm_request(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("periodic", C.c_int32),
+        ("precision", C.c_int32), ("fp16_scale", C.c_float), ("flags", C.c_void_p),
+        ("params", lbm_params), ("steps", C.c_int64),
+    ]
+
+
+LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_DONE, LBM_REQ_CANCELLED, LBM_REQ_FAILED = range(5)
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s (status %d): %s" % (_STATUS.get(status, "?"), status, msg))
@@ -102,6 +120,16 @@ _SIGS = {
     "lbm_layout_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lbm_totals_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.c_int64, C.c_int64, C.c_void_p,
                                      C.c_void_p]),
+    "lbm_server_create": (C.c_int, [C.POINTER(lbm_server_desc), C.POINTER(C.c_void_p)]),
+    "lbm_server_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_server_last_error": (C.c_char_p, [C.c_void_p]),
+    "lbm_server_submit": (C.c_int, [C.c_void_p, C.POINTER(lbm_request), C.POINTER(C.c_int64)]),
+    "lbm_server_tick": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "lbm_server_cells": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "lbm_server_result": (C.c_int, [C.c_void_p, C.c_int64, _dp, _dp]),
+    "lbm_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_server_info": (C.c_int, [C.c_void_p, _dp]),
 }
 
 
@@ -127,6 +155,20 @@ def capi():
 
 def _ptr(a):
     return a.ctypes.data_as(_dp)
+
+
+def make_params(nu=0.0, Re=0.0, u_char=0.0, L_char=0.0, ghost=(1.0, 1.0, 1.0, 1.0), u_in=0.0, d_in=0.0,
+                axis=(-1.0, -1.0), noise_amp=0.0, noise_seed=0, rho_out=1.0, profile="plug"):
+    """An lbm_params filled from lbm_params_default and the given values."""
+    p = lbm_params()
+    capi().lbm_params_default(C.byref(p))
+    p.nu, p.Re, p.u_char, p.L_char = nu, Re, u_char, L_char
+    p.omega3, p.omega4, p.omega5, p.omega6 = (float(g) for g in ghost)
+    p.u_in, p.d_in = u_in, d_in
+    p.axis_x, p.axis_y = axis
+    p.noise_amp, p.noise_seed, p.rho_out = noise_amp, int(noise_seed), rho_out
+    p.inlet_profile = PROFILES[profile] if isinstance(profile, str) else int(profile)
+    return p
 
 
 def make_nozzle(D, d, L_total, L_in=None, L_cone=-1, L_throat=None, half_angle_deg=10.0):
@@ -250,16 +292,9 @@ class Lattice:
         return self.n_active if layout == LBM_LAYOUT_ACTIVE else int(np.prod(self.shape))
 
     # -- parameters and state
-    def set_params(self, nu=0.0, Re=0.0, u_char=0.0, L_char=0.0, ghost=(1.0, 1.0, 1.0, 1.0), u_in=0.0,
-                   d_in=0.0, axis=(-1.0, -1.0), noise_amp=0.0, noise_seed=0, rho_out=1.0, profile="plug"):
-        p = lbm_params()
-        self.lib.lbm_params_default(C.byref(p))
-        p.nu, p.Re, p.u_char, p.L_char = nu, Re, u_char, L_char
-        p.omega3, p.omega4, p.omega5, p.omega6 = (float(g) for g in ghost)
-        p.u_in, p.d_in = u_in, d_in
-        p.axis_x, p.axis_y = axis
-        p.noise_amp, p.noise_seed, p.rho_out = noise_amp, int(noise_seed), rho_out
-        p.inlet_profile = PROFILES[profile] if isinstance(profile, str) else int(profile)
+    def set_params(self, **kw):
+        """lbm_set_params; keywords as make_params."""
+        p = make_params(**kw)
         self._check(self.lib.lbm_set_params(self.ctx, C.byref(p)))
         return self
 
@@ -363,3 +398,91 @@ class Lattice:
         s, b, d = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(self.lib.lbm_layout_info(self.ctx, C.byref(s), C.byref(b), C.byref(d)))
         return dict(slots=s.value, buffer_bytes=b.value, device_bytes=d.value)
+
+
+class Server:
+    """A request server (lbm_server_create .. lbm_server_destroy): continuous
+    batching of many lattices on one GPU.  Memory comes from PyTorch's
+    caching allocator; work runs on a dedicated torch stream."""
+
+    def __init__(self, budget_bytes, max_slots=32, steps_per_tick=32, device=0, stream=None, torch_allocator=True):
+        import torch
+
+        self.lib = capi()
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        self.allocator = TorchAllocator(device, self.stream) if torch_allocator else None
+        d = lbm_server_desc()
+        d.device = device
+        d.stream = C.c_void_p(self.stream.cuda_stream)
+        if self.allocator is not None:
+            d.allocator = self.allocator.struct()
+        d.budget_bytes = int(budget_bytes)
+        d.max_slots = int(max_slots)
+        d.steps_per_tick = int(steps_per_tick)
+        self._desc = d
+        h = C.c_void_p()
+        st = self.lib.lbm_server_create(C.byref(d), C.byref(h))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_server_create")
+        self.h = h
+        self._keep = {}
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, self.lib.lbm_server_last_error(self.h).decode())
+
+    def submit(self, flags, steps, precision="fp32", periodic=0, fp16_scale=0.0, **params):
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        nz, ny, nx = flags.shape
+        r = lbm_request()
+        r.nx, r.ny, r.nz, r.periodic = nx, ny, nz, int(periodic)
+        r.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        r.fp16_scale = float(fp16_scale)
+        r.flags = flags.ctypes.data
+        r.params = make_params(**params)
+        r.steps = int(steps)
+        rid = C.c_int64()
+        self._check(self.lib.lbm_server_submit(self.h, C.byref(r), C.byref(rid)))
+        return rid.value
+
+    def tick(self):
+        run, q = C.c_int32(), C.c_int32()
+        self._check(self.lib.lbm_server_tick(self.h, C.byref(run), C.byref(q)))
+        return run.value, q.value
+
+    def poll(self, rid):
+        st, n = C.c_int32(), C.c_int64()
+        self._check(self.lib.lbm_server_poll(self.h, int(rid), C.byref(st), C.byref(n)))
+        return st.value, n.value
+
+    def cells(self, rid):
+        n = C.c_int64()
+        self._check(self.lib.lbm_server_cells(self.h, int(rid), C.byref(n)))
+        return n.value
+
+    def result(self, rid):
+        n = self.cells(rid)
+        rho, u = np.zeros(n), np.zeros((n, 3))
+        self._check(self.lib.lbm_server_result(self.h, int(rid), _ptr(rho), _ptr(u)))
+        return rho, u
+
+    def cancel(self, rid):
+        self._check(self.lib.lbm_server_cancel(self.h, int(rid)))
+
+    def info(self):
+        out = np.zeros(8)
+        self._check(self.lib.lbm_server_info(self.h, _ptr(out)))
+        keys = ["cell_updates", "ticks", "bytes_in_use", "peak_bytes", "graph_launches", "graph_captures",
+                "finished", "queued"]
+        return dict(zip(keys, out.tolist()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
