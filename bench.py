@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=64)
     return ap.parse_args()
 
 
@@ -273,6 +275,47 @@ class OracleSample:
         return cells / dt / 1e6, dt
 
 
+# ----------------------------------------------------------------- serving
+
+SERVING_D = (8, 24)
+SERVING_STEPS = (200, 2000)
+
+
+def serving_measurement(capacity_mlups, n_requests):
+    """Continuous batching on the seeded request stream (nozzle / pipe runs of
+    throat diameter d, D = 3 d, L = 25 d, Re uniform in 500-6500, FP32 or
+    FP16S with p = 1/2, Poisson arrivals at 1.2 x the measured single-stream
+    FP32 capacity), against the same stream run back to back as plain FP32
+    lattices.  Sizes and step counts are scaled down from the full request
+    mix (d 8-48, 2000-20000 steps) so that the measurement takes seconds."""
+    import torch
+
+    from paper_2204_10566_gb300 import inputs as I
+    from paper_2204_10566_gb300 import lbm, serving
+
+    probe = I.serving_requests(n=n_requests, seed=2204, rate=1.0, d_range=SERVING_D, steps_range=SERVING_STEPS)
+    work = []
+    for s in probe:
+        f = serving.request_geometry(s)
+        work.append(I.active_count(f) * s["steps"])
+    rate = 1.2 * capacity_mlups * 1e6 / (sum(work) / len(work))
+    specs = I.serving_requests(n=n_requests, seed=2204, rate=rate, d_range=SERVING_D, steps_range=SERVING_STEPS)
+    free, _ = torch.cuda.mem_get_info()
+    srv = serving.run_stream([dict(s) for s in specs], budget_bytes=int(0.5 * free), max_slots=32, steps_per_tick=32)
+    b2b = serving.run_back_to_back([dict(s) for s in specs], "fp32")
+    return {
+        "requests": n_requests, "arrival_rate_per_s": rate, "offered_load": 1.2,
+        "stream": "seed 2204; d uniform in %d-%d (D = 3d, L = 25d), Re 500-6500, %d-%d steps, FP32/FP16S, "
+                  "nozzle/pipe; scaled from d 8-48 and 2000-20000 steps" % (SERVING_D + SERVING_STEPS),
+        "p50_s": srv["latency_p50_s"], "p99_s": srv["latency_p99_s"],
+        "aggregate_mlups": srv["mlups"], "makespan_s": srv["makespan_s"],
+        "back_to_back_fp32_mlups": b2b["mlups"], "back_to_back_s": b2b["seconds"],
+        "speedup_vs_back_to_back": srv["mlups"] / b2b["mlups"],
+        "steps_per_tick": 32, "graph_captures": srv["info"]["graph_captures"],
+        "graph_launches": srv["info"]["graph_launches"],
+    }
+
+
 # ------------------------------------------------------------------ arms
 
 def reference_arm(args):
@@ -357,6 +400,9 @@ def ours_arm(args):
             dist.destroy_process_group()
         return
     e2e = e2e_run(lbm, torch, flags, params, periodic, head, args.steps)
+    serve = None
+    if world == 1 and not args.no_serving:
+        serve = serving_measurement(value, args.serving_requests)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         sample = OracleSample(flags, params, periodic, args.cpu_seconds)
@@ -380,6 +426,7 @@ def ours_arm(args):
         "gpu_launches": args.steps * launches_per_step(flags, periodic),
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "serving": serve,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
