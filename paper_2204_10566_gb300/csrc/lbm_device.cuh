@@ -32,7 +32,7 @@
 // Minimum resident blocks per SM requested for the FP32 / FP16S step kernel
 // (caps its registers: 65536 / (threads * blocks)); FP64 is left uncapped.
 #ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 6
+#define LBM_STEP_MIN_BLOCKS 7
 #endif
 
 
@@ -168,9 +168,20 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // SCALED, d holds (f_i - w_i) / in_scale on entry and (f*_i - w_i) * out_scale
 // on exit: the scale is applied to the ten moments and to the eight output
 // coefficients instead of to the 54 populations.
-template <class R, bool SCALED = false>
+// Writes a line of three outputs (cx = -1, 0, +1 of line j) back into d.
+template <class R>
+struct ToArray {
+    R (&d)[27];
+    __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const {
+        d[3 * j] = vm;
+        d[3 * j + 1] = v0;
+        d[3 * j + 2] = vp;
+    }
+};
+
+template <class R, bool SCALED = false, class Out = ToArray<R>>
 __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &ux, R &uy, R &uz,
-                                               R in_scale = R(1), R out_scale = R(1)) {
+                                               R in_scale = R(1), R out_scale = R(1), const Out *sink = nullptr) {
     // x-pass of the moment cascade: per (cy, cz) line, sums weighted by 1, cx, cx^2.
     R s0[9], s1[9], s2[9];
 #pragma unroll
@@ -248,12 +259,14 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
         const R Bw = drho_o * (wy * w1<R>(cz)) + rho_o * D + C0;
         const R Bd = rho_o * E + C0;
         // cx = 0: w = 2/3, d = -ux^2, g1 = -2 ux, g2 = -1
-        d[3 * j + 1] = R(2) / R(3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
+        const R v0 = R(2) / R(3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
         // cx = +-1: w = 1/6, d = (ux^2 +- ux)/2, g1 = ux +- 1/2, g2 = 1/2
         const R S = R(1) / R(6) * Bw + ux2h * Bd + ux * B1 + h * B2;
         const R A = uxh * Bd + h * B1;
-        d[3 * j + 2] = S + A;
-        d[3 * j] = S - A;
+        if (sink)
+            (*sink)(j, S - A, v0, S + A);  // the line's outputs leave registers at once
+        else
+            ToArray<R>{d}(j, S - A, v0, S + A);
     }
 }
 
@@ -517,6 +530,45 @@ __device__ __forceinline__ void store_cell_state(const StepArgs &a, const int (&
     }
 }
 
+// Output sink of the fluid update: each line of three post-collision values
+// goes to the cell's own slots at once, to the ghost slots of the wall links
+// they serve (value i feeds link 26 - i), and across a periodic x face.
+template <int P, bool WIDE, bool RAW>
+struct LineStore {
+    using S = Storage<P>;
+    using T = typename S::T;
+    using R = typename S::R;
+    const StepArgs &a;
+    const int (&nb)[9];
+    int x, slot;
+    uint32_t links;
+    __device__ __forceinline__ void put(int i, int s, R v) const {
+        T *p = static_cast<T *>(a.fout) + elem<WIDE>(i, a.stride, s);
+        if constexpr (RAW)
+            S::store_raw(p, v);
+        else
+            S::store(p, v, R(a.scale));
+    }
+    __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const {
+        put(3 * j, slot, vm);
+        put(3 * j + 1, slot, v0);
+        put(3 * j + 2, slot, vp);
+        const int jl = 8 - j;  // links 26 - i of this line's values sit in line 8 - j
+        if (links & (7u << (3 * jl))) {
+            const R v[3] = {vm, v0, vp};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k = 26 - (3 * j + c);  // wall link k takes value 3j + c
+                if (links & (1u << k)) put(k, nb[k / 3] + x - cx_of(k), v[c]);
+            }
+        }
+        if (a.periodic_x) {  // wrap-around copies read across the periodic x faces
+            if (x == a.nx - 1) put(3 * j + 2, nb[4] - 1, vp);
+            if (x == 0) put(3 * j, nb[4] + a.nx, vm);
+        }
+    }
+};
+
 template <class R>
 __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, R ux, R uy, R uz, double (&hv)[6]) {
     if (a.flags & STEP_STATS) {
@@ -545,11 +597,14 @@ __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lan
     R rho, ux, uy, uz;
     constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
     gather<P, WIDE, RAW>(a, nb, x, d);
-    if constexpr (RAW)
-        collide_ghost1<R, true>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale), R(a.scale));
-    else
+    if constexpr (GHOST1) {
+        const LineStore<P, WIDE, RAW> sink{a, nb, x, slot, links};
+        collide_ghost1<R, RAW, LineStore<P, WIDE, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
+                                                        R(a.scale), &sink);
+    } else {
         collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
-    store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
+        store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
+    }
     record_cell(a, slot, rho, ux, uy, uz, hv);
 }
 
