@@ -169,6 +169,21 @@ def workload_setup(name):
     return w, flags, params, periodic
 
 
+def aggregate_replicas(ms_local, cells_local, steps, dist=None, device="cpu"):
+    """Whole-job numbers of N independent replicas (one lattice per rank):
+    the job takes the slowest rank's time, and its work is the sum of all
+    ranks' cell updates.  Returns (ms_max, total cells, MLUPS)."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(cells_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    ms_max, cells = float(t.item()), float(c.item())
+    return ms_max, cells, cells * steps / (ms_max * 1e-3) / 1e6
+
+
 # --------------------------------------------------------------- our kernels
 
 def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup, dist=None, sampler=None):
@@ -373,11 +388,7 @@ def ours_arm(args):
     sampler = ClockSampler(device) if rank == 0 else None
     n, ms, clocks, info = time_precision(lbm, torch, flags, params, periodic, head, args.steps, args.warmup, dist,
                                          sampler)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * n * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max, _, value = aggregate_replicas(ms, n, args.steps, dist, device="cuda")
     per_launch_s = ms * 1e-3 / max(args.steps, 1)
     alg_bytes = algorithmic_bytes_per_cell(head) * n
     achieved = alg_bytes / per_launch_s / 1e9
