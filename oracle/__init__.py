@@ -66,6 +66,8 @@ def lib():
         L.orc_step.argtypes = [C.POINTER(_Lattice), dp, dp, dp, C.c_int64]
         L.orc_step.restype = C.c_int
         L.orc_field_moments.argtypes = [C.POINTER(_Lattice), dp, dp]
+        L.orc_viscous_stress.argtypes = [dp, C.c_double, dp]
+        L.orc_field_stress.argtypes = [C.POINTER(_Lattice), dp, dp]
         L.orc_totals.argtypes = [C.POINTER(_Lattice), dp, dp]
         L.orc_nee_neighbour.argtypes = [C.POINTER(_Lattice), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
         L.orc_nee_neighbour.restype = C.c_int64
@@ -157,6 +159,13 @@ def collide(f, omega, ghost=(1.0, 1.0, 1.0, 1.0), omega_cons=1.0):
     return fpost, mom
 
 
+def viscous_stress(f, omega):
+    """sigma_ab (xx, yy, zz, xy, xz, yz) of pre-collision populations f."""
+    out = np.zeros(6)
+    lib().orc_viscous_stress(_dp(_vec(f, Q)), float(omega), _dp(out))
+    return out
+
+
 def splitmix64(x):
     return int(lib().orc_splitmix64(C.c_uint64(x & 0xFFFFFFFFFFFFFFFF)))
 
@@ -234,6 +243,32 @@ class Lattice:
         mom = np.zeros((self.ncell, 4))
         lib().orc_field_moments(C.byref(self._L), _dp(self.f), _dp(mom))
         return mom
+
+    def field_stress(self):
+        """(ncell, 6) viscous stress that the next step samples: every fluid
+        cell's from its gathered populations, inlet/outlet nodes their
+        partner's (solid = 0)."""
+        sig = np.zeros((self.ncell, 6))
+        if lib().orc_field_stress(C.byref(self._L), _dp(self.f), _dp(sig)) != 0:
+            raise RuntimeError("boundary node without an interior partner")
+        return sig
+
+    def step_sampled(self, n):
+        """n steps, each one sampled: time averages over those steps of u,
+        u_a u_b (xx, yy, zz, xy, xz, yz), the viscous stress and rho of every
+        box cell, as a dict of arrays (ncell, 3), (ncell, 6), (ncell, 6),
+        (ncell,)."""
+        pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+        acc = dict(u=np.zeros((self.ncell, 3)), uu=np.zeros((self.ncell, 6)), sigma=np.zeros((self.ncell, 6)),
+                   rho=np.zeros(self.ncell))
+        for _ in range(n):
+            acc["sigma"] += self.field_stress()
+            self.step(1)
+            m = self.last_moments
+            acc["u"] += m[:, 1:4]
+            acc["uu"] += np.stack([m[:, 1 + a] * m[:, 1 + b] for a, b in pairs], axis=1)
+            acc["rho"] += m[:, 0]
+        return {k: v / n for k, v in acc.items()}
 
     def totals(self):
         out = np.zeros(4)

@@ -26,7 +26,9 @@
  *   - pull streaming, halfway bounce-back walls (Bouzidi's interpolated
  *     bounce-back at q = 1/2, Sec. 2.2 "Simulation details"), and the
  *     non-equilibrium-extrapolation velocity inlet / constant-pressure outlet
- *     (Sec. 2.2 "Simulation details", inlet profile eq.).
+ *     (Sec. 2.2 "Simulation details", inlet profile eq.);
+ *   - the viscous stress from the pre-collision second-order central Hermite
+ *     moments and the strain-rate relation of Appendix A (Sec. 2.2).
  *
  * Compile with -ffp-contract=off (no fused multiply-add contraction).
  */
@@ -468,6 +470,64 @@ int orc_step(const orc_lattice *L, const double *fin, double *fout, double *mom,
     if (err & 1) return -1;
     if (err & 2) return -2;
     return 0;
+}
+
+/* Viscous stress of one cell from its pre-collision populations f (Sec. 2.2
+ * viscous shear stress sigma_ab = rho nu (d_b u_a + d_a u_b), with the
+ * strain rate of Appendix A taken from the second-order central Hermite
+ * moment, sign as in the non-equilibrium stress):
+ *   a_ab = sum_i f_i ((c_ia - u_a)(c_ib - u_b) - theta0 delta_ab),
+ *   S_ab = -a_ab / (2 rho theta0 tau),  nu = theta0 (tau - 1/2),  tau = 1/omega,
+ *   sigma_ab = 2 rho nu S_ab.
+ * Components in the order xx, yy, zz, xy, xz, yz. */
+void orc_viscous_stress(const double *f, double omega, double sigma[6])
+{
+    static const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+    double mom[4];
+    orc_moments(f, mom);
+    const double rho = mom[0], tau = 1.0 / omega, nu = ORC_THETA0 * (tau - 0.5);
+    for (int k = 0; k < 6; ++k) {
+        double a = 0.0;
+        for (int i = 0; i < ORC_Q; ++i) {
+            int c[3];
+            orc_velocity(i, c);
+            double h = (c[pa[k]] - mom[1 + pa[k]]) * (c[pb[k]] - mom[1 + pb[k]]);
+            if (pa[k] == pb[k]) h -= ORC_THETA0;
+            a += f[i] * h;
+        }
+        const double S = -a / (2.0 * rho * ORC_THETA0 * tau);
+        sigma[k] = 2.0 * rho * nu * S;
+    }
+}
+
+/* Viscous stress field of the step t -> t+1 that starts from the
+ * post-collision state fin at t: every fluid cell's stress from its gathered
+ * (pre-collision) populations; an inlet/outlet node takes the stress of its
+ * interior partner, whose non-equilibrium part the extrapolation copies.
+ * sigma: [b][6], zero at solid cells.  Returns 0, or -1 on a node without
+ * a unique interior partner. */
+int orc_field_stress(const orc_lattice *L, const double *fin, double *sigma)
+{
+    const int64_t ncell = (int64_t)L->nx * L->ny * L->nz;
+    int err = 0;
+    for (int64_t b = 0; b < ncell; ++b) {
+        for (int k = 0; k < 6; ++k) sigma[b * 6 + k] = 0.0;
+        if (L->flags[b] != ORC_FLUID) continue;
+        int x = (int)(b % L->nx), y = (int)((b / L->nx) % L->ny), z = (int)(b / ((int64_t)L->nx * L->ny));
+        double f[ORC_Q];
+        gather(L, fin, x, y, z, f);
+        orc_viscous_stress(f, L->omega, sigma + b * 6);
+    }
+    for (int64_t b = 0; b < ncell; ++b) {
+        int fl = L->flags[b];
+        if (fl != ORC_INLET && fl != ORC_OUTLET) continue;
+        int x = (int)(b % L->nx), y = (int)((b / L->nx) % L->ny), z = (int)(b / ((int64_t)L->nx * L->ny));
+        int n[3];
+        int64_t bf = orc_nee_neighbour(L, x, y, z, n);
+        if (bf < 0) { err = -1; continue; }
+        for (int k = 0; k < 6; ++k) sigma[b * 6 + k] = sigma[bf * 6 + k];
+    }
+    return err;
 }
 
 /* Moments of every active cell of a state (rho, ux, uy, uz per box cell). */

@@ -412,6 +412,71 @@ def test_shear_wave_between_walls(orc):
     assert 3.0 < abs(r8 - 1.0) / abs(r16 - 1.0) < 5.0
 
 
+# ------------------------------------------------------------ viscous stress
+
+def test_viscous_stress_of_equilibrium_is_zero(orc):
+    """The equilibrium has no non-equilibrium second moment: sigma = 0 for
+    any rho, u (a dropped theta0 term or a raw instead of central moment
+    fails on the diagonal)."""
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        rho = 1.0 + 0.1 * rng.standard_normal()
+        u = 0.08 * rng.standard_normal(3)
+        assert np.abs(orc.viscous_stress(orc.equilibrium(rho, u), 1.6)).max() < 1e-15
+
+
+def stress_wave(orc, n, nu, steps, longitudinal):
+    """Periodic sine wave of u_x along y (shear) or x (longitudinal), one
+    box cell thick otherwise.  Returns the ratio of the sampled stress
+    amplitude (sigma_xy resp. sigma_xx on cos) to the Navier-Stokes value
+    rho nu (d_b u_a + d_a u_b) from the velocity amplitude of the same
+    state, and the largest other component relative to it."""
+    k = 2 * np.pi / n
+    c = np.arange(n) + 0.5
+    shape = (1, 2, n) if longitudinal else (1, n, 2)
+    L = orc.Lattice(np.ones(shape, dtype=np.uint8), omega=omega_of_nu(nu), periodic=7)
+    u = np.zeros(shape + (3,))
+    if longitudinal:
+        u[0, :, :, 0] = 0.005 * np.sin(k * c)[None, :]
+    else:
+        u[0, :, :, 0] = 0.01 * np.sin(k * c)[:, None]
+    L.init_equilibrium(1.0, u.reshape(-1, 3))
+    L.step(steps)
+    sig = L.field_stress().reshape(shape + (6,))[0]
+    L.step(1)                                   # the velocity of the same (pre-collision) state
+    m = L.last_moments.reshape(shape + (4,))[0]
+    line = (lambda a: a[0, :]) if longitudinal else (lambda a: a[:, 0])
+    ux, rho = line(m[..., 1]), line(m[..., 0])
+    A = (ux * np.sin(k * c)).sum() / (np.sin(k * c) ** 2).sum()
+    comp = 0 if longitudinal else 3
+    B = (line(sig[..., comp]) * np.cos(k * c)).sum() / (np.cos(k * c) ** 2).sum()
+    expect = (2.0 if longitudinal else 1.0) * rho.mean() * nu * A * k
+    others = [q for q in range(6) if q != comp and not (longitudinal and q in (1, 2))]
+    rest = max(np.abs(line(sig[..., q])).max() for q in others)
+    return B / expect, rest / abs(B)
+
+
+def test_viscous_stress_shear_wave(orc):
+    """Sec. 2.2: sigma_xy = rho nu d_y u_x for a decaying shear wave
+    u_x = U sin(k y), second-order convergent in the resolution; the other
+    components vanish.  A wrong sign, the post- instead of the pre-collision
+    moment (factor 1 - omega) or a missing (1 - omega/2) all fail."""
+    r16, o16 = stress_wave(orc, 16, 0.02, 50, False)
+    r32, o32 = stress_wave(orc, 32, 0.02, 50, False)
+    assert abs(r32 - 1.0) < 5e-3
+    assert 3.0 < abs(r16 - 1.0) / abs(r32 - 1.0) < 5.0
+    assert o16 < 1e-3 and o32 < 1e-3
+
+
+def test_viscous_stress_longitudinal_wave(orc):
+    """Longitudinal (acoustic) wave u_x = U(t) sin(k x): sigma_xx =
+    2 rho nu d_x u_x, the full strain rate of the relation in Appendix A
+    (all six second-order moments relax at omega); off-diagonal terms 0."""
+    r, o = stress_wave(orc, 64, 0.02, 60, True)
+    assert abs(r - 1.0) < 1e-2
+    assert o < 1e-6
+
+
 # --------------------------------------------------------------- inlet/outlet
 
 def duct_flags(n, nz):
