@@ -34,6 +34,7 @@ class _Lattice(C.Structure):
         ("noise_amp", C.c_double), ("rho_out", C.c_double),
         ("seed", C.c_uint64),
         ("profile", C.c_int32), ("nthreads", C.c_int32),
+        ("ramp", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -187,7 +188,7 @@ class Lattice:
 
     def __init__(self, flags, omega, ghost=(1.0, 1.0, 1.0, 1.0), periodic=0,
                  profile=PLUG, u_in=0.0, d_in=None, axis=None, noise_amp=0.0, seed=0,
-                 rho_out=1.0, nthreads=0):
+                 rho_out=1.0, nthreads=0, ramp=0):
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
         assert flags.ndim == 3
         self.flags = flags
@@ -208,6 +209,7 @@ class Lattice:
         L.seed = int(seed)
         L.profile = int(profile)
         L.nthreads = int(nthreads)
+        L.ramp = int(ramp)
         self._L = L
         self.f = np.zeros((self.ncell, Q))
         self.t = 0

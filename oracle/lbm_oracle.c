@@ -61,6 +61,8 @@ typedef struct {
     uint64_t seed;              /* inlet perturbation seed */
     int32_t profile;            /* ORC_PLUG or ORC_PARABOLIC */
     int32_t nthreads;           /* OpenMP threads (0 = runtime default) */
+    int32_t ramp;               /* inlet start-up steps T (0: impulsive start) */
+    int32_t reserved;
 } orc_lattice;
 
 /* ---------------------------------------------------------------- stencil */
@@ -325,7 +327,8 @@ double orc_noise(uint64_t seed, int64_t step, int64_t node, int comp)
 /* Prescribed inlet velocity at node (x, y) with inward unit normal n:
  * speed = u0 (plug) or 2 u0 (1 - 4 r^2 / d0^2) (Sec. 2.2 inlet profile eq.),
  * r measured from the nozzle axis at the cell centre, plus the seeded
- * perturbation noise_amp * u0 * U per component. */
+ * perturbation noise_amp * u0 * U per component, all scaled by the start-up
+ * ramp below. */
 void orc_inlet_velocity(const orc_lattice *L, int x, int y, int64_t node, int64_t step,
                         const int n[3], double u[3])
 {
@@ -338,6 +341,15 @@ void orc_inlet_velocity(const orc_lattice *L, int x, int y, int64_t node, int64_
     for (int a = 0; a < 3; ++a) {
         u[a] = speed * n[a];
         if (L->noise_amp != 0.0) u[a] += L->noise_amp * L->u_in * orc_noise(L->seed, step, node, a);
+    }
+    /* Start-up (the paper does not state one): with ramp T > 0 the whole
+     * prescribed velocity is scaled by the smoothstep r(s) = s^2 (3 - 2 s),
+     * s = step / T, while step < T (r rises from 0 to 1 with zero slope at
+     * both ends). */
+    if (step < L->ramp) {
+        double s = (double)step / (double)L->ramp;
+        double r = s * s * (3.0 - 2.0 * s);
+        for (int a = 0; a < 3; ++a) u[a] *= r;
     }
 }
 
