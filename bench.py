@@ -163,8 +163,7 @@ def workload_setup(name):
         params = dict(nu=w["u0"] * (w["n"] / (2 * 3.141592653589793)) / w["Re"])
         periodic = 7
     else:
-        params = dict(Re=w["Re"], u_char=w["u_throat"], L_char=float(w["d"]), u_in=I.inlet_mean_velocity(w),
-                      d_in=float(w["D"]), profile=w["profile"], noise_amp=w["noise"], noise_seed=w["seed"])
+        params = I.workload_params(name)
         periodic = 0
     return w, flags, params, periodic
 

@@ -108,7 +108,8 @@ typedef struct {
     double rho_out;       /* outlet density (default 1) */
     uint64_t noise_seed;  /* perturbation seed */
     int32_t inlet_profile;/* LBM_PROFILE_PLUG or LBM_PROFILE_PARABOLIC */
-    int32_t reserved;
+    int32_t inlet_ramp;   /* steps T of a smooth inlet start, u_b(t) = u_b r(t/T) with
+                             r(s) = s^2 (3 - 2 s) for t < T (0: impulsive start) */
 } lbm_params;
 
 /* Human-readable name of a status code (static string). */
@@ -224,14 +225,38 @@ lbm_status lbm_stats_begin(lbm_ctx *ctx, int64_t stride);
 lbm_status lbm_stats_end(lbm_ctx *ctx);
 lbm_status lbm_stats_reset(lbm_ctx *ctx);
 
+/* Statistics modes.  LBM_STATS_AXIAL (default): sum u_z and u_z^2, 16 bytes
+ * per slot.  LBM_STATS_FULL: additionally the three velocity components, the
+ * six products u_a u_b, the six components of the viscous stress
+ * sigma_ab = -(1 - omega/2) a_ab from each cell's pre-collision second-order
+ * central Hermite moments a_ab (Appendix A strain-rate relation with the sign
+ * of the non-equilibrium stress; Sec. 2.2 viscous shear stress), and rho;
+ * 144 bytes per slot.  An inlet/outlet node takes the stress of its interior
+ * partner, whose non-equilibrium part it copies.  lbm_stats_set_mode takes
+ * effect at the next lbm_stats_begin; changing the mode while sampling is
+ * LBM_ERR_STATE, and a new mode discards the accumulated samples. */
+#define LBM_STATS_AXIAL 0
+#define LBM_STATS_FULL 1
+#define LBM_STATS_FULL_COMPONENTS 16
+lbm_status lbm_stats_set_mode(lbm_ctx *ctx, int32_t mode);
+
 /* Means over the samples: mean_uz[n] = <u_z>, mean_uzuz[n] = <u_z^2> (either
  * may be NULL), and the sample count.  RMS = sqrt(<u_z^2> - <u_z>^2); the
  * axial Reynolds normal stress is rho (<u_z^2> - <u_z>^2). */
 lbm_status lbm_stats_get(lbm_ctx *ctx, double *mean_uz, double *mean_uzuz, int64_t *n_samples,
                          int32_t layout);
 
+/* Full-mode means, mean[n][16] row-major per cell: <u_x>, <u_y>, <u_z>,
+ * <u_x u_x>, <u_y u_y>, <u_z u_z>, <u_x u_y>, <u_x u_z>, <u_y u_z>,
+ * <sigma_xx>, <sigma_yy>, <sigma_zz>, <sigma_xy>, <sigma_xz>, <sigma_yz>,
+ * <rho> (lattice units; solid cells of the box layout are 0).  The Reynolds
+ * stress tensor (Sec. 2.2) is <rho> (<u_a u_b> - <u_a><u_b>).  mean may be
+ * NULL to read the sample count.  LBM_ERR_STATE if the accumulators were
+ * filled in axial mode. */
+lbm_status lbm_stats_get_full(lbm_ctx *ctx, double *mean, int64_t *n_samples, int32_t layout);
+
 /* Checkpoint: the current populations (native storage precision, bitwise),
- * the step counter and the statistics accumulators.  lbm_restore needs a
+ * the step counter and the statistics accumulators (either mode).  lbm_restore needs a
  * context with the same geometry, precision and scale. */
 lbm_status lbm_checkpoint_size(lbm_ctx *ctx, size_t *bytes);
 lbm_status lbm_checkpoint(lbm_ctx *ctx, void *buf, size_t bytes);

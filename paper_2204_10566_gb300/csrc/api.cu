@@ -42,10 +42,13 @@ struct lbm_ctx {
     lbm_params params{};
     double omega = 0.0;
     bool ghost1 = true;
+    int prefetch_ahead = 0, prefetch_key = -1;  // L2 prefetch lookahead of the fluid kernel, per variant
     int64_t t = 0;
     int64_t check_every = 0;
     bool stats_on = false;
     int64_t stats_stride = 1, stats_start = 0, stats_samples = 0;
+    int32_t stats_mode = LBM_STATS_AXIAL;  // what lbm_stats_begin allocates
+    int stats_ncomp = 0;                   // accumulator rows of d_stats (0: none)
     double health[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -120,7 +123,7 @@ void release_geometry(lbm_ctx *c) {
     dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     dev_free(c, c->d_health, 8 * 8);
     dev_free(c, c->d_status, 256);
-    dev_free(c, c->d_stats, 2 * ns * 8);
+    dev_free(c, c->d_stats, (size_t)c->stats_ncomp * ns * 8);
     c->f[0] = c->f[1] = nullptr;
     c->f_raw[0] = c->f_raw[1] = nullptr;
     c->d_mask = c->d_mask_raw = nullptr;
@@ -132,8 +135,11 @@ void release_geometry(lbm_ctx *c) {
     c->d_health = nullptr;
     c->d_status = nullptr;
     c->d_stats = nullptr;
+    c->stats_ncomp = 0;
     c->has_geom = c->has_state = false;
 }
+
+size_t stats_bytes(const lbm_ctx *c) { return (size_t)c->stats_ncomp * (size_t)c->idx.nslots * 8; }
 
 float fp16_scale(const lbm_ctx *c) { return c->desc.precision == LBM_FP16S ? c->desc.fp16_scale : 1.0f; }
 
@@ -174,7 +180,7 @@ lbm_status reset_state(lbm_ctx *c) {
     c->stats_samples = 0;
     c->stats_on = false;
     CK(cudaMemsetAsync(c->d_status, 0, 4, c->stream), "reset status");
-    if (c->d_stats) CK(cudaMemsetAsync(c->d_stats, 0, 2 * (size_t)c->idx.nslots * 8, c->stream), "reset stats");
+    if (c->d_stats) CK(cudaMemsetAsync(c->d_stats, 0, stats_bytes(c), c->stream), "reset stats");
     c->has_state = true;
     return LBM_OK;
 }
@@ -202,6 +208,7 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.ny_e = c->idx.ny_e;
     a.periodic_x = (c->desc.periodic & LBM_PERIODIC_X) ? 1 : 0;
     a.profile = c->params.inlet_profile;
+    a.inlet_ramp = c->params.inlet_ramp;
     const double gr[4] = {c->params.omega3, c->params.omega4, c->params.omega5, c->params.omega6};
     a.pd.omega = c->omega;
     for (int q = 0; q < 4; ++q) a.pd.ghost[q] = gr[q];
@@ -224,6 +231,13 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.inv_scale = 1.0f / a.scale;
     a.stats = c->d_stats;
     a.partials = c->d_partials;
+    const bool wide = a.stride > MAX_SLOTS_32;
+    const int key = (c->ghost1 ? 2 : 0) + (wide ? 1 : 0);
+    if (c->prefetch_key != key) {
+        c->prefetch_ahead = DISPATCH(c->desc.precision, step_prefetch_ahead, c->ghost1, wide, c->desc.device);
+        c->prefetch_key = key;
+    }
+    a.prefetch_ahead = c->prefetch_ahead;
     a.fin = c->f[c->cur];
     a.fout = c->f[1 - c->cur];
     a.t_new = c->t + 1;
@@ -416,6 +430,7 @@ lbm_status lbm_set_params(lbm_ctx *c, const lbm_params *p) {
     if (p->inlet_profile != LBM_PROFILE_PLUG && p->inlet_profile != LBM_PROFILE_PARABOLIC)
         return fail(c, LBM_ERR_ARG, "unknown inlet profile");
     if (!(p->noise_amp >= 0.0) || !(p->rho_out > 0.0)) return fail(c, LBM_ERR_ARG, "bad noise or rho_out");
+    if (p->inlet_ramp < 0) return fail(c, LBM_ERR_ARG, "negative inlet ramp");
     c->params = *p;
     c->params.nu = nu;
     if (!(c->params.d_in > 0.0)) c->params.d_in = c->desc.nx;
@@ -550,7 +565,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
         const bool check = c->check_every > 0 && t_new % c->check_every == 0;
         if (check) a.flags |= STEP_REDUCE;
         if (c->stats_on && t_new >= c->stats_start && (t_new - c->stats_start) % c->stats_stride == 0) {
-            a.flags |= STEP_STATS;
+            a.flags |= STEP_STATS | (c->stats_ncomp == STATS_FULL ? STEP_STATS_FULL : 0);
             ++c->stats_samples;
         }
         CK(DISPATCH(c->desc.precision, launch_step, a, c->ghost1, c->stream), "step kernel");
@@ -641,17 +656,38 @@ lbm_status lbm_get_health(lbm_ctx *c, double out[6]) {
     return LBM_OK;
 }
 
+// (Re)allocate the accumulators with the row count of the current mode.
+lbm_status stats_alloc(lbm_ctx *c) {
+    const int want = c->stats_mode == LBM_STATS_FULL ? STATS_FULL : STATS_AXIAL;
+    if (c->d_stats && c->stats_ncomp == want) return LBM_OK;
+    dev_free(c, c->d_stats, stats_bytes(c));
+    c->d_stats = nullptr;
+    c->stats_ncomp = 0;
+    c->stats_samples = 0;
+    const size_t bytes = (size_t)want * (size_t)c->idx.nslots * 8;
+    c->d_stats = (double *)dev_alloc(c, bytes);
+    if (!c->d_stats) return fail(c, LBM_ERR_OOM, "statistics allocation failed");
+    c->stats_ncomp = want;
+    CK(cudaMemsetAsync(c->d_stats, 0, bytes, c->stream), "clear stats");
+    return LBM_OK;
+}
+
+lbm_status lbm_stats_set_mode(lbm_ctx *c, int32_t mode) {
+    if (!c) return LBM_ERR_ARG;
+    if (mode != LBM_STATS_AXIAL && mode != LBM_STATS_FULL) return fail(c, LBM_ERR_ARG, "unknown statistics mode");
+    if (c->stats_on && mode != c->stats_mode) return fail(c, LBM_ERR_STATE, "statistics are being sampled");
+    c->stats_mode = mode;
+    c->err.clear();
+    return LBM_OK;
+}
+
 lbm_status lbm_stats_begin(lbm_ctx *c, int64_t stride) {
     lbm_status st = need(c, true, false, true);
     if (st) return st;
     if (stride < 1) return fail(c, LBM_ERR_ARG, "stride must be >= 1");
     DeviceGuard g(c->desc.device);
-    if (!c->d_stats) {
-        c->d_stats = (double *)dev_alloc(c, 2 * (size_t)c->idx.nslots * 8);
-        if (!c->d_stats) return fail(c, LBM_ERR_OOM, "statistics allocation failed");
-        CK(cudaMemsetAsync(c->d_stats, 0, 2 * (size_t)c->idx.nslots * 8, c->stream), "clear stats");
-        c->stats_samples = 0;
-    }
+    st = stats_alloc(c);
+    if (st) return st;
     c->stats_on = true;
     c->stats_stride = stride;
     c->stats_start = c->t + 1;
@@ -668,8 +704,26 @@ lbm_status lbm_stats_reset(lbm_ctx *c) {
     lbm_status st = need(c, true, false, false);
     if (st) return st;
     DeviceGuard g(c->desc.device);
-    if (c->d_stats) CK(cudaMemsetAsync(c->d_stats, 0, 2 * (size_t)c->idx.nslots * 8, c->stream), "clear stats");
+    if (c->d_stats) CK(cudaMemsetAsync(c->d_stats, 0, stats_bytes(c), c->stream), "clear stats");
     c->stats_samples = 0;
+    return LBM_OK;
+}
+
+// Means of the first ncomp accumulator rows, per active cell, to the host
+// ([n_active][ncomp]).
+lbm_status stats_means(lbm_ctx *c, int ncomp, std::vector<double> &h) {
+    const int64_t n = c->idx.n_active;
+    const size_t bytes = (size_t)n * ncomp * 8;
+    h.assign((size_t)n * ncomp, 0.0);
+    if (n == 0) return LBM_OK;
+    double *d = (double *)dev_alloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
+    cudaError_t e = launch_stats_mean(c->d_stats, ncomp, c->d_slot_of_active, n, c->idx.nslots,
+                                      1.0 / (double)c->stats_samples, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, d, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stats readback");
     return LBM_OK;
 }
 
@@ -679,22 +733,14 @@ lbm_status lbm_stats_get(lbm_ctx *c, double *mean_uz, double *mean_uzuz, int64_t
     if (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX) return fail(c, LBM_ERR_ARG, "bad layout");
     if (n_samples) *n_samples = c->stats_samples;
     if (!mean_uz && !mean_uzuz) return LBM_OK;
-    const int64_t n = c->idx.n_active;
     const int64_t total = layout_count(c, layout);
     if (mean_uz) memset(mean_uz, 0, (size_t)total * 8);
     if (mean_uzuz) memset(mean_uzuz, 0, (size_t)total * 8);
     if (!c->d_stats || c->stats_samples == 0) return LBM_OK;
     DeviceGuard g(c->desc.device);
-    const size_t bytes = (size_t)n * 2 * 8;
-    double *d = (double *)dev_alloc(c, bytes);
-    if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
-    std::vector<double> h((size_t)n * 2);
-    cudaError_t e = launch_stats_mean(c->d_stats, c->d_slot_of_active, n, c->idx.nslots,
-                                      1.0 / (double)c->stats_samples, d, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    dev_free(c, d, bytes);
-    if (e != cudaSuccess) return cuda_fail(c, e, "stats readback");
+    std::vector<double> h;
+    st = stats_means(c, STATS_AXIAL, h);
+    if (st) return st;
     for_active(c, layout, [&](int64_t k, int64_t r) {
         if (mean_uz) mean_uz[r] = h[2 * (size_t)k];
         if (mean_uzuz) mean_uzuz[r] = h[2 * (size_t)k + 1];
@@ -702,8 +748,31 @@ lbm_status lbm_stats_get(lbm_ctx *c, double *mean_uz, double *mean_uzuz, int64_t
     return LBM_OK;
 }
 
+lbm_status lbm_stats_get_full(lbm_ctx *c, double *mean, int64_t *n_samples, int32_t layout) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX) return fail(c, LBM_ERR_ARG, "bad layout");
+    if (n_samples) *n_samples = c->stats_samples;
+    if (!mean) return LBM_OK;
+    if (c->stats_ncomp != STATS_FULL && c->stats_samples > 0)
+        return fail(c, LBM_ERR_STATE, "the accumulators hold axial statistics only");
+    const int64_t total = layout_count(c, layout);
+    memset(mean, 0, (size_t)total * LBM_STATS_FULL_COMPONENTS * 8);
+    if (!c->d_stats || c->stats_samples == 0) return LBM_OK;
+    DeviceGuard g(c->desc.device);
+    std::vector<double> h;
+    st = stats_means(c, STATS_FULL, h);
+    if (st) return st;
+    for_active(c, layout, [&](int64_t k, int64_t r) {
+        for (int q = 0; q < LBM_STATS_FULL_COMPONENTS; ++q)
+            mean[(size_t)r * LBM_STATS_FULL_COMPONENTS + q] = h[(size_t)k * STATS_FULL + STATS_AXIAL + q];
+    });
+    return LBM_OK;
+}
+
 // Checkpoint image: header, then the current population buffer (native
-// storage, bitwise), then the two statistics accumulators if allocated.
+// storage, bitwise), then the statistics accumulators if allocated
+// (has_stats holds their row count: 0, 2 or 18).
 struct CkptHeader {
     uint64_t magic;
     int32_t version, precision, nx, ny, nz, periodic;
@@ -713,12 +782,13 @@ struct CkptHeader {
     int32_t stats_on, reserved;
 };
 static const uint64_t CKPT_MAGIC = 0x4c424d3237434b50ULL;  // "LBM27CKP"
+static const int32_t CKPT_VERSION = 2;
 
 lbm_status lbm_checkpoint_size(lbm_ctx *c, size_t *bytes) {
     lbm_status st = need(c, true, false, true);
     if (st) return st;
     if (!bytes) return fail(c, LBM_ERR_ARG, "NULL output");
-    *bytes = sizeof(CkptHeader) + pop_bytes(c) + (c->d_stats ? 2 * (size_t)c->idx.nslots * 8 : 0);
+    *bytes = sizeof(CkptHeader) + pop_bytes(c) + stats_bytes(c);
     return LBM_OK;
 }
 
@@ -730,14 +800,14 @@ lbm_status lbm_checkpoint(lbm_ctx *c, void *buf, size_t bytes) {
     DeviceGuard g(c->desc.device);
     CkptHeader h{};
     h.magic = CKPT_MAGIC;
-    h.version = 1;
+    h.version = CKPT_VERSION;
     h.precision = c->desc.precision;
     h.nx = c->desc.nx;
     h.ny = c->desc.ny;
     h.nz = c->desc.nz;
     h.periodic = c->desc.periodic;
     h.scale = fp16_scale(c);
-    h.has_stats = c->d_stats != nullptr;
+    h.has_stats = c->d_stats ? c->stats_ncomp : 0;
     h.nslots = c->idx.nslots;
     h.n_active = c->idx.n_active;
     h.t = c->t;
@@ -751,8 +821,7 @@ lbm_status lbm_checkpoint(lbm_ctx *c, void *buf, size_t bytes) {
     CK(cudaMemcpyAsync(p, c->f[c->cur], pop_bytes(c), cudaMemcpyDeviceToHost, c->stream), "checkpoint f");
     p += pop_bytes(c);
     if (c->d_stats)
-        CK(cudaMemcpyAsync(p, c->d_stats, 2 * (size_t)c->idx.nslots * 8, cudaMemcpyDeviceToHost, c->stream),
-           "checkpoint stats");
+        CK(cudaMemcpyAsync(p, c->d_stats, stats_bytes(c), cudaMemcpyDeviceToHost, c->stream), "checkpoint stats");
     CK(cudaStreamSynchronize(c->stream), "sync checkpoint");
     return LBM_OK;
 }
@@ -763,12 +832,14 @@ lbm_status lbm_restore(lbm_ctx *c, const void *buf, size_t bytes) {
     if (!buf || bytes < sizeof(CkptHeader)) return fail(c, LBM_ERR_ARG, "checkpoint too small");
     CkptHeader h;
     memcpy(&h, buf, sizeof h);
-    if (h.magic != CKPT_MAGIC || h.version != 1) return fail(c, LBM_ERR_ARG, "not a checkpoint image");
+    if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION) return fail(c, LBM_ERR_ARG, "not a checkpoint image");
+    if (h.has_stats != 0 && h.has_stats != STATS_AXIAL && h.has_stats != STATS_FULL)
+        return fail(c, LBM_ERR_ARG, "checkpoint statistics block is malformed");
     if (h.precision != c->desc.precision || h.nx != c->desc.nx || h.ny != c->desc.ny || h.nz != c->desc.nz ||
         h.periodic != c->desc.periodic || h.scale != fp16_scale(c) || h.nslots != c->idx.nslots ||
         h.n_active != c->idx.n_active)
         return fail(c, LBM_ERR_ARG, "checkpoint does not match this context's geometry or precision");
-    const size_t need_bytes = sizeof h + pop_bytes(c) + (h.has_stats ? 2 * (size_t)h.nslots * 8 : 0);
+    const size_t need_bytes = sizeof h + pop_bytes(c) + (size_t)h.has_stats * (size_t)h.nslots * 8;
     if (bytes < need_bytes) return fail(c, LBM_ERR_ARG, "checkpoint truncated");
     DeviceGuard g(c->desc.device);
     const char *p = static_cast<const char *>(buf) + sizeof h;
@@ -776,12 +847,11 @@ lbm_status lbm_restore(lbm_ctx *c, const void *buf, size_t bytes) {
     CK(cudaMemcpyAsync(c->f[0], p, pop_bytes(c), cudaMemcpyHostToDevice, c->stream), "restore f");
     p += pop_bytes(c);
     if (h.has_stats) {
-        if (!c->d_stats) {
-            c->d_stats = (double *)dev_alloc(c, 2 * (size_t)c->idx.nslots * 8);
-            if (!c->d_stats) return fail(c, LBM_ERR_OOM, "statistics allocation failed");
-        }
-        CK(cudaMemcpyAsync(c->d_stats, p, 2 * (size_t)h.nslots * 8, cudaMemcpyHostToDevice, c->stream),
-           "restore stats");
+        c->stats_on = false;
+        c->stats_mode = h.has_stats == STATS_FULL ? LBM_STATS_FULL : LBM_STATS_AXIAL;
+        st = stats_alloc(c);
+        if (st) return st;
+        CK(cudaMemcpyAsync(c->d_stats, p, stats_bytes(c), cudaMemcpyHostToDevice, c->stream), "restore stats");
     }
     CK(cudaMemsetAsync(c->d_status, 0, 4, c->stream), "reset status");
     CK(cudaStreamSynchronize(c->stream), "sync restore");

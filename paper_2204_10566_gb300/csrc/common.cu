@@ -49,19 +49,18 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *health,
     return cudaGetLastError();
 }
 
-__global__ void k_stats_mean(const double *stats, const int32_t *slot_of_active, int64_t n, int64_t stride,
-                             double inv_n, double *out2) {
+__global__ void k_stats_mean(const double *stats, int ncomp, const int32_t *slot_of_active, int64_t n, int64_t stride,
+                             double inv_n, double *out) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int slot = slot_of_active[k];
-    out2[2 * k] = stats[slot] * inv_n;
-    out2[2 * k + 1] = stats[stride + slot] * inv_n;
+    for (int q = 0; q < ncomp; ++q) out[(size_t)ncomp * k + q] = stats[(size_t)q * stride + slot] * inv_n;
 }
 
-cudaError_t launch_stats_mean(const double *stats, const int32_t *slot_of_active, int64_t n, int64_t stride,
-                              double inv_n, double *out2, cudaStream_t s) {
+cudaError_t launch_stats_mean(const double *stats, int ncomp, const int32_t *slot_of_active, int64_t n, int64_t stride,
+                              double inv_n, double *out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_stats_mean<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(stats, slot_of_active, n, stride, inv_n, out2);
+    k_stats_mean<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(stats, ncomp, slot_of_active, n, stride, inv_n, out);
     return cudaGetLastError();
 }
 

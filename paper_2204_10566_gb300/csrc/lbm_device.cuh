@@ -34,6 +34,11 @@
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 7
 #endif
+// L2 prefetch lookahead of the fluid kernel, in percent of the blocks
+// resident on the device (0 disables the prefetch).
+#ifndef LBM_PREFETCH_AHEAD_PCT
+#define LBM_PREFETCH_AHEAD_PCT 200
+#endif
 
 
 namespace lbm {
@@ -158,6 +163,22 @@ __device__ __forceinline__ void add_eq_difference(R rb, R uxb, R uyb, R uzb, R r
     }
 }
 
+// ------------------------------------------------------ viscous stress
+
+// Viscous stress of a cell from its pre-collision second-order central
+// Hermite moments a_ab = sum_i ((c - u)_a (c - u)_b - theta0 delta_ab) f_i
+// (Appendix A strain-rate relation, with the sign of the non-equilibrium
+// stress): sigma_ab = 2 rho nu S_ab = -(1 - omega/2) a_ab, accumulated in
+// FP64 on statistics sample steps (Sec. 2.2 viscous shear stress).
+template <class R>
+__device__ __forceinline__ void record_stress(const StepArgs &a, int slot, R omega, const R (&a2)[6]) {
+    if ((a.flags & (STEP_STATS | STEP_STATS_FULL)) != (STEP_STATS | STEP_STATS_FULL)) return;
+    const double f = -(1.0 - 0.5 * (double)omega);
+    double *p = a.stats + 11 * (int64_t)a.stride + slot;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) p[q * a.stride] += f * (double)a2[q];
+}
+
 // --------------------------------------------------------------- collision
 
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
@@ -172,11 +193,22 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 template <class R>
 struct ToArray {
     R (&d)[27];
+    __device__ __forceinline__ void moments(R, const R (&)[6]) const {}
     __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const {
         d[3 * j] = vm;
         d[3 * j + 1] = v0;
         d[3 * j + 2] = vp;
     }
+};
+
+// ToArray that also records the viscous stress of the cell at `slot`.
+template <class R>
+struct ToArrayStress {
+    const StepArgs &a;
+    int slot;
+    R (&d)[27];
+    __device__ __forceinline__ void moments(R omega, const R (&a2)[6]) const { record_stress(a, slot, omega, a2); }
+    __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const { ToArray<R>{d}(j, vm, v0, vp); }
 };
 
 template <class R, bool SCALED = false, class Out = ToArray<R>>
@@ -232,12 +264,15 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
     const R th = theta0<R>();
     const R k = SCALED ? (R(1) - omega) * out_scale : R(1) - omega;
     const R rho_o = SCALED ? rho * out_scale : rho, drho_o = SCALED ? drho * out_scale : drho;
-    const R Axx = k * (pxx - rho * ux * ux - th * drho);
-    const R Ayy = k * (pyy - rho * uy * uy - th * drho);
-    const R Azz = k * (pzz - rho * uz * uz - th * drho);
-    const R Axy = k * (pxy - rho * ux * uy);
-    const R Axz = k * (pxz - rho * ux * uz);
-    const R Ayz = k * (pyz - rho * uy * uz);
+    const R a2[6] = {pxx - rho * ux * ux - th * drho, pyy - rho * uy * uy - th * drho, pzz - rho * uz * uz - th * drho,
+                     pxy - rho * ux * uy,            pxz - rho * ux * uz,            pyz - rho * uy * uz};
+    if (sink) sink->moments(omega, a2);
+    const R Axx = k * a2[0];
+    const R Ayy = k * a2[1];
+    const R Azz = k * a2[2];
+    const R Axy = k * a2[3];
+    const R Axz = k * a2[4];
+    const R Ayz = k * a2[5];
     // Inverse: f* = rho prod g0 + sum over the six relaxed second-order moments
     // of A_m prod_a g_{m_a}; orders 1 and 3..6 are zero after relaxation.
     // Per (cy, cz) line the x-dependence is spanned by {w, d, g1, g2}(cx):
@@ -282,9 +317,9 @@ __device__ __forceinline__ R hfwd(int k, int c, R u) {
 //   e0 = 1, e1 = -u, e2 = u^2 (the central moments of the weights);
 //   A* = A + S (A^eq - A), A^eq = (rho, 0, ..., 0);
 //   f* - w = T^-1 (A* - e).
-template <class R>
+template <class R, class Sink = ToArray<R>>
 __device__ __forceinline__ void collide_general(R (&d)[27], R omega, const R (&ghost)[4], R &rho, R &ux,
-                                                R &uy, R &uz) {
+                                                R &uy, R &uz, const Sink *sink = nullptr) {
     R drho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
@@ -324,6 +359,11 @@ __device__ __forceinline__ void collide_general(R (&d)[27], R omega, const R (&g
             for (int k = 0; k < 3; ++k)
                 a[kx + 3 * ky + 9 * k] = hfwd<R>(k, -1, uz) * b[kx + 3 * ky] + hfwd<R>(k, 0, uz) * b[kx + 3 * ky + 9] +
                                          hfwd<R>(k, 1, uz) * b[kx + 3 * ky + 18];
+    if (sink) {  // second-order central Hermite moments A_m = e_m + a_m
+        const R a2[6] = {ux * ux + a[2], uy * uy + a[6], uz * uz + a[18],
+                         ux * uy + a[4], ux * uz + a[10], uy * uz + a[12]};
+        sink->moments(omega, a2);
+    }
     // relax; work with D_m = A*_m - e_m
 #pragma unroll
     for (int m = 0; m < 27; ++m) {
@@ -476,14 +516,18 @@ __device__ __forceinline__ const FlowParams<double> &flow<double>(const StepArgs
 template <>
 __device__ __forceinline__ const FlowParams<float> &flow<float>(const StepArgs &a) { return a.pf; }
 
+// Collision of d in place; the viscous stress is recorded at stress_slot.
 template <int P, bool GHOST1>
 __device__ __forceinline__ void collide(typename Storage<P>::R (&d)[27], const FlowParams<typename Storage<P>::R> &fp,
                                         typename Storage<P>::R &rho, typename Storage<P>::R &ux,
-                                        typename Storage<P>::R &uy, typename Storage<P>::R &uz) {
+                                        typename Storage<P>::R &uy, typename Storage<P>::R &uz, const StepArgs &a,
+                                        int stress_slot) {
+    using R = typename Storage<P>::R;
+    const ToArrayStress<R> sink{a, stress_slot, d};
     if (GHOST1)
-        collide_ghost1(d, fp.omega, rho, ux, uy, uz);
+        collide_ghost1<R, false, ToArrayStress<R>>(d, fp.omega, rho, ux, uy, uz, R(1), R(1), &sink);
     else
-        collide_general(d, fp.omega, fp.ghost, rho, ux, uy, uz);
+        collide_general<R, ToArrayStress<R>>(d, fp.omega, fp.ghost, rho, ux, uy, uz, &sink);
 }
 
 // Post-collision state of one cell is in d; write it to its own slot, the
@@ -549,6 +593,7 @@ struct LineStore {
         else
             S::store(p, v, R(a.scale));
     }
+    __device__ __forceinline__ void moments(R omega, const R (&a2)[6]) const { record_stress(a, slot, omega, a2); }
     __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const {
         put(3 * j, slot, vm);
         put(3 * j + 1, slot, v0);
@@ -575,6 +620,16 @@ __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, 
         const double w = (double)uz;
         a.stats[slot] += w;
         a.stats[a.stride + slot] += w * w;
+        if (a.flags & STEP_STATS_FULL) {  // time averages of u, u u and rho (Sec. 2.2)
+            const double u[3] = {(double)ux, (double)uy, (double)uz};
+            const double uu[6] = {u[0] * u[0], u[1] * u[1], u[2] * u[2], u[0] * u[1], u[0] * u[2], u[1] * u[2]};
+            double *p = a.stats + 2 * (int64_t)a.stride + slot;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) p[q * a.stride] += u[q];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) p[(3 + q) * a.stride] += uu[q];
+            p[15 * a.stride] += (double)rho;
+        }
     }
     if (a.flags & STEP_REDUCE) health_values(rho, ux, uy, uz, hv);
 }
@@ -602,7 +657,7 @@ __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lan
         collide_ghost1<R, RAW, LineStore<P, WIDE, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
                                                         R(a.scale), &sink);
     } else {
-        collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz);
+        collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz, a, slot);
         store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
     }
     record_cell(a, slot, rho, ux, uy, uz, hv);
@@ -630,7 +685,7 @@ __device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (
     R d[27];
     R rf, uxf, uyf, uzf, rho, ux, uy, uz;
     gather<P, WIDE>(a, nbf, xf, d);
-    collide<P, GHOST1>(d, fp, rf, uxf, uyf, uzf);
+    collide<P, GHOST1>(d, fp, rf, uxf, uyf, uzf, a, slot);  // the node takes its partner's stress
     if (type == TYPE_INLET) {
         R speed = fp.u_in;
         if (a.profile == LBM_PROFILE_PARABOLIC) {
@@ -649,6 +704,12 @@ __device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (
             uy += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 1);
             uz += amp * inlet_noise<R>(a.seed, a.t_new, node_id, 2);
         }
+        if (a.t_new < a.inlet_ramp) {  // smooth start: u_b r(t), r = s^2 (3 - 2 s), s = t / T
+            const R sr = R(a.t_new) / R(a.inlet_ramp), r = sr * sr * (R(3) - R(2) * sr);
+            ux *= r;
+            uy *= r;
+            uz *= r;
+        }
     } else {
         rho = fp.rho_out;
         ux = uxf;
@@ -662,13 +723,51 @@ __device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (
     record_cell(a, slot, rho, ux, uy, uz, hv);
 }
 
-// One time step of every fluid cell of one lattice.
+// Largest span one population's L2 prefetch may cover (bytes).
+constexpr int64_t PREFETCH_MAX_BYTES = 16384;
+
+// L2 prefetch of the pull sources of fluid block tb, population i.  The
+// block's chunks cover rows r0..r1 in storage order, and the rows that
+// population i pulls from, r + (cy, cz) for every r, are stored back to back
+// in the same order, so its sources (slots nb_r[j] + x - cx) lie in one span
+// from the first chunk's first lane to the last chunk's last lane.  The span
+// is widened to 16-byte bounds, which stay inside the buffer margins.  Spans
+// that wrap around a periodic y or z face (reversed or very long) are
+// skipped: a prefetch only moves data, never changes a result.
+template <int P>
+__device__ __forceinline__ void prefetch_block_sources(const StepArgs &a, int tb, int i) {
+    using T = typename Storage<P>::T;
+    const int c0 = tb * (STEP_THREADS / CHUNK);
+    if (tb < 0 || c0 >= a.nchunks) return;
+    const int c1 = min(c0 + STEP_THREADS / CHUNK, a.nchunks) - 1;
+    const int2 h0 = __ldg(a.chunks + c0), h1 = __ldg(a.chunks + c1);
+    const int j = i / 3, cx = i % 3 - 1;
+    const int *rn = reinterpret_cast<const int *>(a.row_nb);
+    const int b0 = __ldg(rn + (int64_t)ROW_RECORD_INTS * h0.x + j);
+    const int b1 = __ldg(rn + (int64_t)ROW_RECORD_INTS * h1.x + j);
+    const int64_t s0 = (int64_t)b0 + (int)((uint32_t)h0.y & CHUNK_X0_MASK) - cx;
+    const int64_t s1 = (int64_t)b1 + (int)((uint32_t)h1.y & CHUNK_X0_MASK) + CHUNK - cx;
+    if (s1 <= s0 || (s1 - s0) * (int64_t)sizeof(T) > PREFETCH_MAX_BYTES) return;
+    const char *arr = static_cast<const char *>(a.fin) + (int64_t)i * a.stride * (int64_t)sizeof(T);
+    const uintptr_t lo = (uintptr_t)(arr + s0 * (int64_t)sizeof(T)) & ~(uintptr_t)15;
+    const uintptr_t hi = ((uintptr_t)(arr + s1 * (int64_t)sizeof(T)) + 15) & ~(uintptr_t)15;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
+// One time step of every fluid cell of one lattice.  The last warp of each
+// block also prefetches the pull sources of block blockIdx.x +
+// a.prefetch_ahead into L2 (one bulk prefetch per population), so that the
+// gathers of later blocks find their rows in L2 instead of waiting on HBM.
 template <int P, bool GHOST1, bool WIDE>
 __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
     const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
     const int chunk = gt / CHUNK;
     double hv[6] = {0, 0, 0, 0, 0, 0};
     if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE>(a, chunk, gt % CHUNK, hv);
+    if (a.prefetch_ahead > 0) {
+        const int i = (int)threadIdx.x - (STEP_THREADS - 32);
+        if (i >= 0 && i < 27) prefetch_block_sources<P>(a, (int)blockIdx.x + a.prefetch_ahead, i);
+    }
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
 
@@ -859,6 +958,23 @@ int step_fluid_blocks(int32_t nchunks) {
     return step_blocks(nchunks);
 }
 
+template <int P>
+int step_prefetch_ahead(bool ghost1, bool wide, int device) {
+    int per_sm = 0, sms = 0;
+    cudaError_t e;
+    if (ghost1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, true, true> : k_step<P, true, false>,
+                                                          STEP_THREADS, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, false, true> : k_step<P, false, false>,
+                                                          STEP_THREADS, 0);
+    if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int)((int64_t)per_sm * sms * LBM_PREFETCH_AHEAD_PCT / 100);
+}
+
 template <int P, bool G, bool WD>
 void launch_fluid(const StepArgs &a, cudaStream_t s) {
     k_step<P, G, WD><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
@@ -942,6 +1058,7 @@ cudaError_t launch_init_eq(void *f, const int32_t *soa, int64_t n, int64_t strid
 #define LBM_INSTANTIATE(P)                                                                                         \
     template cudaError_t launch_step<P>(const StepArgs &, bool, cudaStream_t);                                     \
     template int step_fluid_blocks<P>(int32_t);                                                                     \
+    template int step_prefetch_ahead<P>(bool, bool, int);                                                          \
     template cudaError_t launch_reduce<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \
                                           cudaStream_t);                                                           \
     template cudaError_t launch_fill_ghosts<P>(void *, const uint32_t *, const int2 *, const int4 *, int32_t,      \

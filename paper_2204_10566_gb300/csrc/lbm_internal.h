@@ -40,7 +40,13 @@ enum : uint32_t {
     DIR_SHIFT = 29,
 };
 
-enum : int { STEP_REDUCE = 1, STEP_STATS = 2 };
+enum : int { STEP_REDUCE = 1, STEP_STATS = 2, STEP_STATS_FULL = 4 };
+
+// Statistics accumulators, [components][slots] doubles: 0 sum u_z, 1 sum u_z^2
+// (always), and with full statistics 2..4 sum u, 5..10 sum u_a u_b
+// (xx, yy, zz, xy, xz, yz), 11..16 sum sigma_ab (same order), 17 sum rho.
+constexpr int STATS_AXIAL = 2;
+constexpr int STATS_FULL = 18;
 
 // Chunk records (int2): x = row, y = x0 | fluid-lane mask << CHUNK_LANES_SHIFT.
 // The lane mask lets the gather start without waiting for the per-cell link
@@ -87,8 +93,10 @@ struct alignas(16) StepArgs {
     int64_t t_new;
     float scale, inv_scale;
     int64_t stride;         // elements between two population arrays (= slot count)
-    double *stats;          // [2][stride]: sum u_z, sum u_z^2
+    double *stats;          // [STATS_AXIAL or STATS_FULL][stride] accumulators
     double *partials;       // [gridDim.x][REDUCE_SLOTS]
+    int32_t prefetch_ahead; // fluid blocks between a block and the one whose sources it prefetches to L2 (0: off)
+    int32_t inlet_ramp;     // steps over which the inlet velocity rises from 0 (0: impulsive start)
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).
@@ -98,6 +106,10 @@ constexpr int64_t MAX_SLOTS_32 = (int64_t)0xFFFFFFFFu / 27 - 64;
 
 template <int P>
 cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s);
+// L2 prefetch lookahead of the fluid kernel in blocks: a fixed share of the
+// blocks resident on the device at once (occupancy x SM count); 0 = off.
+template <int P>
+int step_prefetch_ahead(bool ghost1, bool wide, int device);
 // Blocks of one step's fluid kernel (partial-sum slots it writes).
 template <int P>
 int step_fluid_blocks(int32_t nchunks);
@@ -128,8 +140,8 @@ int fluid_blocks(int32_t nchunks);
 int node_blocks(int64_t n);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *health, uint32_t *status,
                             cudaStream_t s);
-cudaError_t launch_stats_mean(const double *stats, const int32_t *slot_of_active, int64_t n,
-                              int64_t stride, double inv_n, double *out2, cudaStream_t s);
+cudaError_t launch_stats_mean(const double *stats, int ncomp, const int32_t *slot_of_active, int64_t n,
+                              int64_t stride, double inv_n, double *out, cudaStream_t s);
 
 // Host-side sparse index (built by geometry.cpp).
 struct HostIndex {

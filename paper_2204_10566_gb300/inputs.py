@@ -86,12 +86,16 @@ WORKLOADS = {
     "nozzle_re500_24x24x160": dict(kind="nozzle", D=24, d=8, L_total=160, Re=500.0, u_throat=0.05,
                                    profile="plug", noise=0.0, seed=0, steps=200),
     # Re 3500 transitional nozzle: D = 96, d = 32, parabolic inlet + 1 % noise.
+    # The two jet workloads start the inlet smoothly over `ramp` steps: an
+    # impulsive start sends a pressure pulse through the nozzle that, with
+    # almost no bulk damping at tau -> 1/2, blew up most Re 6500 runs near
+    # the cone-throat junction around step 6000.
     "nozzle_re3500_96x96x800": dict(kind="nozzle", D=96, d=32, L_total=800, Re=3500.0, u_throat=0.05,
-                                    profile="parabolic", noise=0.01, seed=1, steps=20000),
+                                    profile="parabolic", noise=0.01, seed=1, steps=20000, ramp=8000),
     # Re 6500 under-resolved turbulent nozzle: D = 144, d = 48, parabolic + 2 % noise.
     "nozzle_re6500_144x144x1200": dict(kind="nozzle", D=144, d=48, L_total=1200, Re=6500.0,
                                        u_throat=0.05, profile="parabolic", noise=0.02, seed=2,
-                                       steps=50000),
+                                       steps=50000, ramp=8000),
     # Periodic Taylor-Green vortex, 256^3, u0 = 0.04.
     "tgv_256": dict(kind="tgv", n=256, u0=0.04, Re=1600.0, steps=1000),
 }
@@ -111,6 +115,16 @@ def workload_flags(name):
 def inlet_mean_velocity(w):
     """Mean inlet velocity u0 = u_throat (d/D)^2 (Sec. 2.2 throat-velocity relation)."""
     return w["u_throat"] * (w["d"] / w["D"]) ** 2
+
+
+def workload_params(name):
+    """Flow parameters of a nozzle or pipe workload, as keyword arguments of
+    the library's parameter set (Re on the throat, throat mean velocity and
+    diameter as the characteristic scales)."""
+    w = WORKLOADS[name]
+    return dict(Re=w["Re"], u_char=w["u_throat"], L_char=float(w["d"]), u_in=inlet_mean_velocity(w),
+                d_in=float(w["D"]), profile=w["profile"], noise_amp=w["noise"], noise_seed=w["seed"],
+                inlet_ramp=w.get("ramp", 0))
 
 
 # ------------------------------------------------------------- random fields

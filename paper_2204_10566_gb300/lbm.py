@@ -23,6 +23,8 @@ LBM_SOLID, LBM_FLUID, LBM_INLET, LBM_OUTLET = 0, 1, 2, 3
 LBM_PROFILE_PLUG, LBM_PROFILE_PARABOLIC = 0, 1
 LBM_LAYOUT_ACTIVE, LBM_LAYOUT_BOX = 0, 1
 LBM_PERIODIC_X, LBM_PERIODIC_Y, LBM_PERIODIC_Z = 1, 2, 4
+LBM_STATS_AXIAL, LBM_STATS_FULL = 0, 1
+LBM_STATS_FULL_COMPONENTS = 16
 
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S}
 PROFILES = {"plug": LBM_PROFILE_PLUG, "parabolic": LBM_PROFILE_PARABOLIC}
@@ -52,7 +54,7 @@ class lbm_params(C.Structure):
         ("u_in", C.c_double), ("d_in", C.c_double), ("axis_x", C.c_double), ("axis_y", C.c_double),
         ("noise_amp", C.c_double), ("rho_out", C.c_double),
         ("noise_seed", C.c_uint64),
-        ("inlet_profile", C.c_int32), ("reserved", C.c_int32),
+        ("inlet_profile", C.c_int32), ("inlet_ramp", C.c_int32),
     ]
 
 
@@ -114,6 +116,8 @@ _SIGS = {
     "lbm_stats_end": (C.c_int, [C.c_void_p]),
     "lbm_stats_reset": (C.c_int, [C.c_void_p]),
     "lbm_stats_get": (C.c_int, [C.c_void_p, _dp, _dp, C.POINTER(C.c_int64), C.c_int32]),
+    "lbm_stats_set_mode": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lbm_stats_get_full": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_int32]),
     "lbm_checkpoint_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lbm_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lbm_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -158,7 +162,7 @@ def _ptr(a):
 
 
 def make_params(nu=0.0, Re=0.0, u_char=0.0, L_char=0.0, ghost=(1.0, 1.0, 1.0, 1.0), u_in=0.0, d_in=0.0,
-                axis=(-1.0, -1.0), noise_amp=0.0, noise_seed=0, rho_out=1.0, profile="plug"):
+                axis=(-1.0, -1.0), noise_amp=0.0, noise_seed=0, rho_out=1.0, profile="plug", inlet_ramp=0):
     """An lbm_params filled from lbm_params_default and the given values."""
     p = lbm_params()
     capi().lbm_params_default(C.byref(p))
@@ -168,6 +172,7 @@ def make_params(nu=0.0, Re=0.0, u_char=0.0, L_char=0.0, ghost=(1.0, 1.0, 1.0, 1.
     p.axis_x, p.axis_y = axis
     p.noise_amp, p.noise_seed, p.rho_out = noise_amp, int(noise_seed), rho_out
     p.inlet_profile = PROFILES[profile] if isinstance(profile, str) else int(profile)
+    p.inlet_ramp = int(inlet_ramp)
     return p
 
 
@@ -362,7 +367,12 @@ class Lattice:
         self._check(self.lib.lbm_get_health(self.ctx, _ptr(out)))
         return out
 
-    def stats_begin(self, stride=1):
+    def stats_begin(self, stride=1, full=None):
+        """Start sampling every stride-th step.  full=True selects the full
+        statistics (u, u u, viscous stress, rho), full=False the axial ones;
+        None keeps the current mode."""
+        if full is not None:
+            self._check(self.lib.lbm_stats_set_mode(self.ctx, LBM_STATS_FULL if full else LBM_STATS_AXIAL))
         self._check(self.lib.lbm_stats_begin(self.ctx, int(stride)))
         return self
 
@@ -381,6 +391,20 @@ class Lattice:
         k = C.c_int64()
         self._check(self.lib.lbm_stats_get(self.ctx, _ptr(m1), _ptr(m2), C.byref(k), layout))
         return m1, m2, k.value
+
+    def stats_get_full(self, layout=LBM_LAYOUT_ACTIVE):
+        """Full-mode time averages as a dict of arrays: u (n, 3), uu (n, 6),
+        sigma (n, 6) (components xx, yy, zz, xy, xz, yz), rho (n,), the
+        Reynolds stress reynolds = <rho> (<u_a u_b> - <u_a><u_b>) (n, 6), and
+        the sample count."""
+        n = self._count(layout)
+        m = np.zeros((n, LBM_STATS_FULL_COMPONENTS))
+        k = C.c_int64()
+        self._check(self.lib.lbm_stats_get_full(self.ctx, _ptr(m), C.byref(k), layout))
+        u, uu, sigma, rho = m[:, 0:3], m[:, 3:9], m[:, 9:15], m[:, 15]
+        pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+        reynolds = rho[:, None] * (uu - np.stack([u[:, a] * u[:, b] for a, b in pairs], axis=1))
+        return dict(u=u, uu=uu, sigma=sigma, rho=rho, reynolds=reynolds, samples=k.value)
 
     def checkpoint(self):
         n = C.c_size_t()

@@ -4,7 +4,8 @@ runs, and report time-to-result percentiles and aggregate throughput.
 
 Each request is a nozzle (or straight pipe) flow: throat diameter d, pipe
 diameter D = 3 d, length 25 d, Reynolds number Re on the throat (throat mean
-velocity 0.05 lattice units), parabolic inlet with 1 % noise, a step count
+velocity 0.05 lattice units), parabolic inlet with 1 % noise started smoothly
+over a quarter of the run (at most 8000 steps), a step count
 and a storage precision (FP32 or FP16-shifted).  The scheduling itself (slot
 table, admission by device footprint, batched launches, CUDA graph) lives in
 the C++ server; this module only submits requests when they arrive, ticks
@@ -29,7 +30,8 @@ def request_geometry(spec):
 def request_params(spec):
     d, D = spec["d"], spec["D"]
     return dict(Re=spec["Re"], u_char=U_THROAT, L_char=float(d), u_in=U_THROAT * (d / D) ** 2, d_in=float(D),
-                profile="parabolic", noise_amp=0.01, noise_seed=1000 + spec["id"])
+                profile="parabolic", noise_amp=0.01, noise_seed=1000 + spec["id"],
+                inlet_ramp=min(8000, spec["steps"] // 4))
 
 
 def run_stream(specs, budget_bytes, max_slots=32, steps_per_tick=32, precision=None, time_scale=1.0):

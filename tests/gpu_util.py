@@ -14,20 +14,20 @@ def omega_of_nu(nu):
 
 
 def oracle_lattice(orc, flags, nu, periodic=0, ghost=(1.0, 1.0, 1.0, 1.0), profile="plug", u_in=0.0, d_in=None,
-                   noise_amp=0.0, seed=0, rho_out=1.0):
+                   noise_amp=0.0, seed=0, rho_out=1.0, ramp=0):
     nz, ny, nx = flags.shape
     return orc.Lattice(flags, omega_of_nu(nu), ghost=ghost, periodic=periodic,
                        profile=orc.PLUG if profile == "plug" else orc.PARABOLIC, u_in=u_in,
                        d_in=d_in if d_in else nx, axis=(nx / 2.0, ny / 2.0), noise_amp=noise_amp, seed=seed,
-                       rho_out=rho_out)
+                       rho_out=rho_out, ramp=ramp)
 
 
 def gpu_lattice(lbm, flags, precision, nu, periodic=0, ghost=(1.0, 1.0, 1.0, 1.0), profile="plug", u_in=0.0,
-                d_in=None, noise_amp=0.0, seed=0, rho_out=1.0, fp16_scale=0.0):
+                d_in=None, noise_amp=0.0, seed=0, rho_out=1.0, fp16_scale=0.0, ramp=0):
     nz, ny, nx = flags.shape
     G = lbm.Lattice(flags, precision, periodic=periodic, fp16_scale=fp16_scale)
     G.set_params(nu=nu, ghost=ghost, u_in=u_in, d_in=d_in if d_in else nx, profile=profile,
-                 noise_amp=noise_amp, noise_seed=seed, rho_out=rho_out)
+                 noise_amp=noise_amp, noise_seed=seed, rho_out=rho_out, inlet_ramp=ramp)
     return G
 
 
@@ -102,6 +102,9 @@ def oracle_cell_update(orc, f, flags, x, y, z, periodic, omega, ghost=(1.0, 1.0,
         if inlet["noise_amp"]:
             ub = ub + np.array([inlet["noise_amp"] * inlet["u_in"] * orc.noise(inlet["seed"], t_new, node, a)
                                 for a in range(3)])
+        if t_new < inlet.get("ramp", 0):
+            s = t_new / inlet["ramp"]
+            ub = ub * (s * s * (3.0 - 2.0 * s))
         rb = rf
     else:
         ub, rb = uf, inlet["rho_out"]

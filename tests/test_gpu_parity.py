@@ -77,14 +77,15 @@ def test_walls_ragged_rows(orc, lbm, precision, tol):
         assert np.abs(u[act] - mo[act, 1:]).max() < 1e-14
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
-def test_nee_duct_parabolic_noise(orc, lbm, precision):
-    """Velocity inlet (parabolic profile + seeded noise) and pressure outlet by
-    non-equilibrium extrapolation, periodic cross-section."""
+@pytest.mark.parametrize("precision,ramp", [("fp64", 0), ("fp32", 0), ("fp16s", 0), ("fp64", 4), ("fp32", 4)])
+def test_nee_duct_parabolic_noise(orc, lbm, precision, ramp):
+    """Velocity inlet (parabolic profile + seeded noise, impulsive or ramped
+    start) and pressure outlet by non-equilibrium extrapolation, periodic
+    cross-section."""
     flags = np.ones((12, 8, 8), dtype=np.uint8)
     flags[0] = 2
     flags[-1] = 3
-    bc = dict(profile="parabolic", u_in=0.03, d_in=8.0, noise_amp=0.02, seed=77, rho_out=1.001)
+    bc = dict(profile="parabolic", u_in=0.03, d_in=8.0, noise_amp=0.02, seed=77, rho_out=1.001, ramp=ramp)
     O, G, act = run_both(orc, lbm, flags, precision, 6, nu=0.03, periodic=3, **bc)
     fg = G.get_populations(BOX)
     rho, u = G.moments(BOX)
@@ -275,7 +276,7 @@ def test_full_size_sampled_cells(orc, lbm, name, precision):
     flags = I.workload_flags(name)
     nu = w["u_throat"] * w["d"] / w["Re"]
     bc = dict(profile=w["profile"], u_in=I.inlet_mean_velocity(w), d_in=float(w["D"]), noise_amp=w["noise"],
-              seed=w["seed"], rho_out=1.0)
+              seed=w["seed"], rho_out=1.0, ramp=w.get("ramp", 0))
     G = gpu_lattice(lbm, flags, precision, nu, **bc)
     n = G.n_active
     G.init_fields(I.random_density_field(n, 0.01, 5), I.random_velocity_field(n, 0.02, 6))
@@ -288,7 +289,7 @@ def test_full_size_sampled_cells(orc, lbm, name, precision):
     pick += list(np.nonzero(flags.reshape(-1) == 2)[0][:20]) + list(np.nonzero(flags.reshape(-1) == 3)[0][:20])
     nz, ny, nx = flags.shape
     inlet = dict(profile=w["profile"], u_in=bc["u_in"], d_in=float(w["D"]), axis=(nx / 2, ny / 2),
-                 noise_amp=w["noise"], seed=w["seed"], rho_out=1.0)
+                 noise_amp=w["noise"], seed=w["seed"], rho_out=1.0, ramp=bc["ramp"])
     f2 = G.get_populations(BOX)
     errs = []
     for b in pick:
