@@ -167,6 +167,29 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
             }
     out.n_active = (int64_t)out.slot_of_active.size();
     if (out.n_active == 0) return "geometry has no active cells";
+
+    // Non-active slots: bit i marks population array i as read there (the
+    // ghost slot of a wall link, or a periodic-x copy).  The fluid kernel
+    // writes every other array of a non-fluid chunk lane with filler, so that
+    // the 32-byte sectors at row ends are written whole.
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int fl = flags[box_index(x, y, z, nx, ny)];
+                if (fl == LBM_SOLID) continue;
+                const int64_t r = row_of(y, z);
+                if (px && x == nx - 1)
+                    for (int i = 2; i < 27; i += 3) out.mask[(size_t)(base[r] - 1)] |= 1u << i;
+                if (px && x == 0)
+                    for (int i = 0; i < 27; i += 3) out.mask[(size_t)(base[r] + nx)] |= 1u << i;
+                if (fl != LBM_FLUID) continue;
+                for (int i = 0; i < 27; ++i) {
+                    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+                    int ys, zs;
+                    if (source(x - cx, y - cy, z - cz, ys, zs) == LBM_SOLID)
+                        out.mask[(size_t)(base[row_of(ys, zs)] + x - cx)] |= 1u << i;
+                }
+            }
     return "";
 }
 
@@ -194,7 +217,8 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
             if (flags[bx] != LBM_FLUID || seen[bx]++) return "chunk lane is not a unique fluid cell";
         }
     }
-    // pulls of every fluid cell land on stored slots
+    // pulls of every fluid cell land on stored slots: an active cell's, or a
+    // non-active slot that marks the pulled array as read (never filled)
     for (int64_t k = 0; k < ix.n_active; ++k) {
         const int64_t bx = ix.box_of_active[k];
         if (flags[bx] != LBM_FLUID) continue;
@@ -204,10 +228,25 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
         for (int i = 0; i < 27; ++i) {
             const int64_t s = (int64_t)nb[i / 3] + x - (i % 3 - 1);
             if (s < 0 || s >= ns) return "pull slot outside the buffer";
+            const uint32_t m = ix.mask[(size_t)s];
+            if (((m >> TYPE_SHIFT) & 3u) == TYPE_PAD && !((m >> i) & 1u)) return "pulled slot not marked as read";
         }
     }
     for (int64_t b = 0; b < (int64_t)seen.size(); ++b)
         if ((flags[b] == LBM_FLUID) != (seen[b] == 1)) return "fluid cell not in exactly one chunk lane";
+    // every lane of every chunk (fluid or not) loads its 27 pull slots: they
+    // must lie inside the buffer and its margins
+    const int64_t margin = buffer_margin(nx);
+    for (const int2 &c : ix.chunks) {
+        const int32_t *nb = &ix.row_nb[(size_t)c.x * ROW_RECORD_INTS];
+        const int x0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
+        for (int l = 0; l < CHUNK; ++l)
+            for (int i = 0; i < 27; ++i) {
+                const int64_t s = (int64_t)nb[i / 3] + x0 + l - (i % 3 - 1);
+                if (s < -margin || s >= ns + margin) return "chunk lane pull outside the buffer margins";
+            }
+        if ((int64_t)nb[4] + x0 < 0 || (int64_t)nb[4] + x0 + CHUNK > ns) return "chunk slots outside the buffer";
+    }
     for (const int4 &n : ix.bnodes)
         if (n.z < 0 || n.z >= ns || ix.row_nb[(size_t)n.y * ROW_RECORD_INTS + 4] + n.x != n.z) return "boundary node";
     (void)periodic;

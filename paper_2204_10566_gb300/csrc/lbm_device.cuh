@@ -577,6 +577,10 @@ __device__ __forceinline__ void store_cell_state(const StepArgs &a, const int (&
 // Output sink of the fluid update: each line of three post-collision values
 // goes to the cell's own slots at once, to the ghost slots of the wall links
 // they serve (value i feeds link 26 - i), and across a periodic x face.
+// own: bit i set = store value i in the cell's own slot; bit 31 = the lane is
+// a fluid cell (the other lanes only fill unread arrays, see fluid_cell).
+constexpr uint32_t OWN_FLUID = 1u << 31;
+
 template <int P, bool WIDE, bool RAW>
 struct LineStore {
     using S = Storage<P>;
@@ -585,7 +589,7 @@ struct LineStore {
     const StepArgs &a;
     const int (&nb)[9];
     int x, slot;
-    uint32_t links;
+    uint32_t links, own;
     __device__ __forceinline__ void put(int i, int s, R v) const {
         T *p = static_cast<T *>(a.fout) + elem<WIDE>(i, a.stride, s);
         if constexpr (RAW)
@@ -593,11 +597,13 @@ struct LineStore {
         else
             S::store(p, v, R(a.scale));
     }
-    __device__ __forceinline__ void moments(R omega, const R (&a2)[6]) const { record_stress(a, slot, omega, a2); }
+    __device__ __forceinline__ void moments(R omega, const R (&a2)[6]) const {
+        if (own & OWN_FLUID) record_stress(a, slot, omega, a2);
+    }
     __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const {
-        put(3 * j, slot, vm);
-        put(3 * j + 1, slot, v0);
-        put(3 * j + 2, slot, vp);
+        if (own & (1u << (3 * j))) put(3 * j, slot, vm);
+        if (own & (2u << (3 * j))) put(3 * j + 1, slot, v0);
+        if (own & (4u << (3 * j))) put(3 * j + 2, slot, vp);
         const int jl = 8 - j;  // links 26 - i of this line's values sit in line 8 - j
         if (links & (7u << (3 * jl))) {
             const R v[3] = {vm, v0, vp};
@@ -607,7 +613,7 @@ struct LineStore {
                 if (links & (1u << k)) put(k, nb[k / 3] + x - cx_of(k), v[c]);
             }
         }
-        if (a.periodic_x) {  // wrap-around copies read across the periodic x faces
+        if (a.periodic_x && (own & OWN_FLUID)) {  // wrap-around copies read across the periodic x faces
             if (x == a.nx - 1) put(3 * j + 2, nb[4] - 1, vp);
             if (x == 0) put(3 * j, nb[4] + a.nx, vm);
         }
@@ -636,31 +642,41 @@ __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, 
 
 // Update of the fluid cell in lane `lane` of chunk `chunk` (Sec. 2.1
 // evolution equation, pull form): gather, collide, store, refill the ghost
-// slots of its wall links.
+// slots of its wall links.  The chunk's other lanes run the same instruction
+// stream on whatever their pull slots hold (all inside the buffer and its
+// margins) and store the result only into the arrays that nobody reads at
+// their slot (link word of a padding / ghost slot: bit i = array i is read
+// there; nothing at inlet/outlet slots).  This completes the 32-byte sectors
+// at the row ends, which the memory system would otherwise have to read
+// back before writing them, at no extra instructions per warp.
 template <int P, bool GHOST1, bool WIDE>
 __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lane, double (&hv)[6]) {
     using R = typename Storage<P>::R;
     const int2 ch = __ldg(a.chunks + chunk);
     const uint32_t cw = (uint32_t)ch.y;
-    if (!((cw >> (CHUNK_LANES_SHIFT + lane)) & 1u)) return;
+    const bool fluid = (cw >> (CHUNK_LANES_SHIFT + lane)) & 1u;
     const int x = (int)(cw & CHUNK_X0_MASK) + lane;
     int nb[9];
     load_row(a.row_nb, ch.x, nb);
     const int slot = nb[4] + x;
-    const uint32_t links = __ldg(a.mask + slot) & LINK_MASK;  // needed after the collision only
+    const uint32_t m = __ldg(a.mask + slot);  // needed after the collision only
+    const uint32_t links = fluid ? (m & LINK_MASK) : 0u;
+    const uint32_t own = fluid ? (LINK_MASK | OWN_FLUID)
+                               : (((m >> TYPE_SHIFT) & 3u) == TYPE_PAD ? (~m & LINK_MASK) : 0u);
     R d[27];
     R rho, ux, uy, uz;
     constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
     gather<P, WIDE, RAW>(a, nb, x, d);
     if constexpr (GHOST1) {
-        const LineStore<P, WIDE, RAW> sink{a, nb, x, slot, links};
+        const LineStore<P, WIDE, RAW> sink{a, nb, x, slot, links, own};
         collide_ghost1<R, RAW, LineStore<P, WIDE, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
                                                         R(a.scale), &sink);
     } else {
+        if (!fluid) return;
         collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz, a, slot);
         store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
     }
-    record_cell(a, slot, rho, ux, uy, uz, hv);
+    if (fluid) record_cell(a, slot, rho, ux, uy, uz, hv);
 }
 
 // Update of inlet/outlet node k: non-equilibrium extrapolation (Sec. 2.2)

@@ -28,6 +28,9 @@ constexpr int REDUCE_SLOTS = 8;  // doubles per block partial
 //                reflected population f*_{26-i} into the ghost slot that
 //                stands at x - c_i in population array i, so that the next
 //                step's pull of population i is the halfway bounce-back.
+//                At a padding / ghost slot, bit i instead marks population
+//                array i as read there (a wall link's ghost value or a
+//                periodic copy); the other arrays take filler.
 //   bits 27..28: node type (0 fluid, 1 inlet, 2 outlet, 3 padding / ghost)
 //   bits 29..31: inlet/outlet partner direction (0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z)
 enum : uint32_t {
