@@ -35,9 +35,13 @@
 #define LBM_STEP_MIN_BLOCKS 7
 #endif
 // L2 prefetch lookahead of the fluid kernel, in percent of the blocks
-// resident on the device (0 disables the prefetch).
+// resident on the device (0 disables the prefetch).  FP16S is issue-bound
+// rather than waiting on memory, and runs faster without it.
 #ifndef LBM_PREFETCH_AHEAD_PCT
 #define LBM_PREFETCH_AHEAD_PCT 200
+#endif
+#ifndef LBM_PREFETCH_AHEAD_PCT_FP16S
+#define LBM_PREFETCH_AHEAD_PCT_FP16S 0
 #endif
 
 
@@ -184,6 +188,92 @@ __device__ __forceinline__ void record_stress(const StepArgs &a, int slot, R ome
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// Packed FP32 (two values per instruction, sm_100 and later) for the inverse
+// transform of the rate-1 collision.  Off: -DLBM_PACKED_F32=0.
+#ifndef LBM_PACKED_F32
+#define LBM_PACKED_F32 1
+#endif
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// Shared inputs of the per-line inverse (see collide_ghost1).
+struct PairCoef {
+    float Axx, Ayy, Azz, Axy, Axz, Ayz, rho_o, drho_o, ux, ux2h, uxh;
+};
+
+// One line (cy, cz) of the inverse: f*_i - w_i for cx = -1, 0, +1.
+template <class R, int J, class Out>
+__device__ __forceinline__ void inverse_line(R Axx, R Ayy, R Azz, R Axy, R Axz, R Ayz, R rho_o, R drho_o, R ux, R ux2h,
+                                             R uxh, const Axis<R> &Y, const Axis<R> &Z, R (&d)[27], const Out *sink) {
+    constexpr int cy = J % 3 - 1, cz = J / 3 - 1;
+    const R h = R(0.5);
+    const R wy = w1<R>(cy);
+    const R gy0 = Y.g0[cy + 1], gz0 = Z.g0[cz + 1], gy1 = Y.g1[cy + 1], gz1 = Z.g1[cz + 1];
+    const R E = gy0 * gz0;
+    const R D = Y.d[cy + 1] * gz0 + wy * Z.d[cz + 1];
+    const R C0 = Ayy * g2<R>(cy) * gz0 + Azz * gy0 * g2<R>(cz) + Ayz * gy1 * gz1;
+    const R B1 = Axy * gy1 * gz0 + Axz * gy0 * gz1;
+    const R B2 = Axx * E;
+    const R Bw = drho_o * (wy * w1<R>(cz)) + rho_o * D + C0;
+    const R Bd = rho_o * E + C0;
+    const R v0 = R(2) / R(3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
+    const R S = R(1) / R(6) * Bw + ux2h * Bd + ux * B1 + h * B2;
+    const R A = uxh * Bd + h * B1;
+    if (sink)
+        (*sink)(J, S - A, v0, S + A);
+    else {
+        d[3 * J] = S - A;
+        d[3 * J + 1] = v0;
+        d[3 * J + 2] = S + A;
+    }
+}
+
+// Two lines of the inverse at once.  The pair differs along one axis ("v",
+// c = -1 in .x and +1 in .y) and shares the other ("f"); the line formulas
+// are symmetric in y and z once the diagonal and mixed second-order
+// coefficients are relabelled, so one routine serves both kinds of pair:
+//   E = g0v g0f,  D = dv g0f + (1/6) df,
+//   C0 = Avv (1/2) g0f + Aff g2f g0v + Ayz g1f g1v,
+//   B1 = Axv g0f g1v + Axf g1f g0v,  B2 = Axx E,
+// with the same Bw, Bd, v0, S, A as the scalar line.
+template <int JA, int JB, class Out>
+__device__ __forceinline__ void inverse_pair(const PairCoef &c, const Axis<float> &Y, const Axis<float> &Z,
+                                             float (&d)[27], const Out *sink) {
+    constexpr bool YV = (JA / 3) == (JB / 3);  // same cz: y varies
+    constexpr int cf = YV ? JA / 3 - 1 : JA % 3 - 1;  // fixed axis velocity
+    const Axis<float> &V = YV ? Y : Z;
+    const Axis<float> &F = YV ? Z : Y;
+    const float Avv = YV ? c.Ayy : c.Azz, Aff = YV ? c.Azz : c.Ayy;
+    const float Axv = YV ? c.Axy : c.Axz, Axf = YV ? c.Axz : c.Axy;
+    const float f0 = F.g0[cf + 1], f1 = F.g1[cf + 1], fd = F.d[cf + 1], fw = w1<float>(cf), fg2 = g2<float>(cf);
+    const float2 v0_ = make_float2(V.g0[0], V.g0[2]), v1_ = make_float2(V.g1[0], V.g1[2]);
+    const float2 vd = make_float2(V.d[0], V.d[2]);
+    const float2 E = __fmul2_rn(v0_, bc2(f0));
+    const float2 D = __ffma2_rn(vd, bc2(f0), bc2(fd * (1.0f / 6.0f)));
+    const float2 C0 = __ffma2_rn(v1_, bc2(c.Ayz * f1), __ffma2_rn(v0_, bc2(Aff * fg2), bc2(0.5f * Avv * f0)));
+    const float2 hB1 = __ffma2_rn(v1_, bc2(0.5f * Axv * f0), __fmul2_rn(v0_, bc2(0.5f * Axf * f1)));
+    const float2 nB2 = __fmul2_rn(v0_, bc2(-c.Axx * f0));
+    const float2 hB2 = __fmul2_rn(v0_, bc2(0.5f * c.Axx * f0));
+    const float2 Bw = __ffma2_rn(bc2(c.rho_o), D, __fadd2_rn(C0, bc2(c.drho_o * (fw * (1.0f / 6.0f)))));
+    const float2 Bd = __ffma2_rn(bc2(c.rho_o), E, C0);
+    const float2 t = __ffma2_rn(bc2(c.ux2h), Bd, __fmul2_rn(bc2(2.0f * c.ux), hB1));
+    const float2 o0 = __ffma2_rn(bc2(2.0f / 3.0f), Bw, __ffma2_rn(bc2(-2.0f), t, nB2));
+    const float2 S = __ffma2_rn(bc2(1.0f / 6.0f), Bw, __fadd2_rn(t, hB2));
+    const float2 A = __ffma2_rn(bc2(c.uxh), Bd, hB1);
+    const float2 om = __ffma2_rn(bc2(-1.0f), A, S), op = __fadd2_rn(S, A);
+    if (sink) {
+        (*sink)(JA, om.x, o0.x, op.x);
+        (*sink)(JB, om.y, o0.y, op.y);
+    } else {
+        d[3 * JA] = om.x;
+        d[3 * JA + 1] = o0.x;
+        d[3 * JA + 2] = op.x;
+        d[3 * JB] = om.y;
+        d[3 * JB + 1] = o0.y;
+        d[3 * JB + 2] = op.y;
+    }
+}
+
 // Collision with the default ghost rates (all 1).  d holds f_i - w_i on entry
 // and f*_i - w_i on exit; rho, u receive the (conserved) moments.  With
 // SCALED, d holds (f_i - w_i) / in_scale on entry and (f*_i - w_i) * out_scale
@@ -281,6 +371,19 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
     const Axis<R> Y(uy), Z(uz);
     const R h = R(0.5);
     const R ux2h = h * ux * ux, uxh = h * ux;
+#if LBM_PACKED_F32
+    if constexpr (std::is_same<R, float>::value) {
+        // Lines in pairs on the packed FP32 pipe (two lanes per instruction):
+        // (cy = -1, +1) at each cz, then (cz = -1, +1) at cy = 0; line 4 alone.
+        const PairCoef c{Axx, Ayy, Azz, Axy, Axz, Ayz, rho_o, drho_o, ux, ux2h, uxh};
+        inverse_pair<0, 2>(c, Y, Z, d, sink);
+        inverse_pair<3, 5>(c, Y, Z, d, sink);
+        inverse_pair<6, 8>(c, Y, Z, d, sink);
+        inverse_pair<1, 7>(c, Y, Z, d, sink);
+        inverse_line<R, 4>(Axx, Ayy, Azz, Axy, Axz, Ayz, rho_o, drho_o, ux, ux2h, uxh, Y, Z, d, sink);
+        return;
+    }
+#endif
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
         const int cy = j % 3 - 1, cz = j / 3 - 1;
@@ -988,7 +1091,8 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
         cudaGetLastError();
         return 0;
     }
-    return (int)((int64_t)per_sm * sms * LBM_PREFETCH_AHEAD_PCT / 100);
+    const int pct = P == 2 ? LBM_PREFETCH_AHEAD_PCT_FP16S : LBM_PREFETCH_AHEAD_PCT;
+    return (int)((int64_t)per_sm * sms * pct / 100);
 }
 
 template <int P, bool G, bool WD>
