@@ -35,6 +35,7 @@ class _Lattice(C.Structure):
         ("seed", C.c_uint64),
         ("profile", C.c_int32), ("nthreads", C.c_int32),
         ("ramp", C.c_int32), ("reserved", C.c_int32),
+        ("wall_q", C.c_void_p),
     ]
 
 
@@ -188,7 +189,7 @@ class Lattice:
 
     def __init__(self, flags, omega, ghost=(1.0, 1.0, 1.0, 1.0), periodic=0,
                  profile=PLUG, u_in=0.0, d_in=None, axis=None, noise_amp=0.0, seed=0,
-                 rho_out=1.0, nthreads=0, ramp=0):
+                 rho_out=1.0, nthreads=0, ramp=0, wall_q=None):
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
         assert flags.ndim == 3
         self.flags = flags
@@ -210,6 +211,9 @@ class Lattice:
         L.profile = int(profile)
         L.nthreads = int(nthreads)
         L.ramp = int(ramp)
+        if wall_q is not None:  # [ncell][27] uint8, q = k / 256 per wall link
+            self._wall_q = np.ascontiguousarray(wall_q, dtype=np.uint8).reshape(self.ncell, Q)
+            L.wall_q = self._wall_q.ctypes.data
         self._L = L
         self.f = np.zeros((self.ncell, Q))
         self.t = 0

@@ -23,8 +23,9 @@
  *   - the collision f* = f + T^-1 S T (f^eq - f) with T_{m,i} = H_m(c_i - u)
  *     (Sec. 2.1, MRT evolution eq. and central Hermite moment eq.), the inverse
  *     applied by Gaussian elimination with partial pivoting on the dense 27x27 T;
- *   - pull streaming, halfway bounce-back walls (Bouzidi's interpolated
- *     bounce-back at q = 1/2, Sec. 2.2 "Simulation details"), and the
+ *   - pull streaming, walls by Bouzidi's interpolated bounce-back (halfway
+ *     bounce-back, q = 1/2, unless per-link wall distances are given;
+ *     Sec. 2.2 "Simulation details"), and the
  *     non-equilibrium-extrapolation velocity inlet / constant-pressure outlet
  *     (Sec. 2.2 "Simulation details", inlet profile eq.);
  *   - the viscous stress from the pre-collision second-order central Hermite
@@ -63,6 +64,8 @@ typedef struct {
     int32_t nthreads;           /* OpenMP threads (0 = runtime default) */
     int32_t ramp;               /* inlet start-up steps T (0: impulsive start) */
     int32_t reserved;
+    const uint8_t *wall_q;      /* optional [b][27]: wall distance q = k/256 of wall link i
+                                   of fluid cell b (NULL: q = 1/2 on every link) */
 } orc_lattice;
 
 /* ---------------------------------------------------------------- stencil */
@@ -399,9 +402,16 @@ int64_t orc_nee_neighbour(const orc_lattice *L, int x, int y, int z, int n[3])
     return count == 1 ? found : -1;
 }
 
-/* Pull-stream gather for cell (x,y,z): f_i(x, t+1) = f*_i(x - c_i, t), or the
- * halfway bounce-back f*_{opp(i)}(x, t) when x - c_i is solid or outside a
- * non-periodic box (Bouzidi's scheme at q = 1/2). */
+/* Pull-stream gather for cell (x,y,z): f_i(x, t+1) = f*_i(x - c_i, t), or,
+ * when x - c_i is solid or outside a non-periodic box, the population
+ * reflected by the wall that cuts the link between x and x - c_i
+ * (Sec. 2.2, Bouzidi's interpolated bounce-back).  With ib the opposite of
+ * i (the direction that points from x at the wall) and q in (0, 1] the
+ * wall's distance from x as a fraction of the link:
+ *   q <  1/2:  f_i(x, t+1) = 2q f*_ib(x, t) + (1 - 2q) f*_ib(x + c_i, t),
+ *   q >= 1/2:  f_i(x, t+1) = f*_ib(x, t) / (2q) + (1 - 1/(2q)) f*_i(x, t);
+ * q = 1/2 is the halfway bounce-back f*_ib(x, t).  When x + c_i is itself
+ * solid the first form has no second point and the halfway value is used. */
 static void gather(const orc_lattice *L, const double *fin, int x, int y, int z, double *f)
 {
     int64_t self = box_index(L, x, y, z);
@@ -410,10 +420,23 @@ static void gather(const orc_lattice *L, const double *fin, int x, int y, int z,
         orc_velocity(i, c);
         int64_t src = -1;
         int fl = flag_at(L, x - c[0], y - c[1], z - c[2], &src);
-        if (fl == ORC_SOLID)
-            f[i] = fin[self * ORC_Q + (ORC_Q - 1 - i)];
-        else
+        if (fl != ORC_SOLID) {
             f[i] = fin[src * ORC_Q + i];
+            continue;
+        }
+        const int ib = ORC_Q - 1 - i;
+        double fi = fin[self * ORC_Q + ib];
+        if (L->wall_q) {
+            const double q = L->wall_q[self * ORC_Q + i] / 256.0;
+            if (q < 0.5) {
+                int64_t nbr = -1;
+                if (flag_at(L, x + c[0], y + c[1], z + c[2], &nbr) != ORC_SOLID)
+                    fi = 2.0 * q * fin[self * ORC_Q + ib] + (1.0 - 2.0 * q) * fin[nbr * ORC_Q + ib];
+            } else {
+                fi = fin[self * ORC_Q + ib] / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * fin[self * ORC_Q + i];
+            }
+        }
+        f[i] = fi;
     }
 }
 

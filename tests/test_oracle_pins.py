@@ -525,6 +525,49 @@ def test_square_duct_poiseuille_profile(orc):
     assert np.ptp(flux) < 1e-6 * flux.mean()
 
 
+def channel_wall_fit(orc, n, nz, nu, ylo, yhi, use_q=True, steps=3000):
+    """Developed flow between two plates behind a plug inlet, one cell deep
+    (x periodic), with the plates at y = ylo and y = yhi (cell faces at 0 and
+    n; cell centres at j + 1/2).  Every link that leaves the box through a
+    plate is cut at q = 0.5 - ylo (bottom) or yhi - (n - 0.5) (top).  Returns
+    the plate positions read off a parabola fitted to the mid-plane u_z."""
+    flags = duct_flags(1, nz)[:, :1, :1].repeat(n, axis=1)
+    wq = np.full((flags.size, Q), 128, dtype=np.uint8)
+    c = vel()
+    for z in range(nz):
+        for j, qv, cy in ((0, 0.5 - ylo, 1), (n - 1, yhi - (n - 0.5), -1)):
+            for i in range(Q):
+                if c[i, 1] == cy:
+                    wq[z * n + j, i] = int(round(qv * 256))
+    L = orc.Lattice(flags, omega=omega_of_nu(nu), periodic=1, u_in=0.01, wall_q=wq if use_q else None)
+    L.init_equilibrium(1.0, [0.0, 0.0, 0.0])
+    L.step(steps)
+    uz = L.moments()[:, 3].reshape(nz, n)[nz // 2]
+    y = np.arange(n) + 0.5
+    return np.sort(np.roots(np.polyfit(y, uz, 2)).real)
+
+
+def test_interpolated_bounce_back_places_the_walls(orc):
+    """Sec. 2.2 walls: Bouzidi's interpolated bounce-back puts a plane wall
+    where its link fractions q say, for both of its branches (q < 1/2 and
+    q >= 1/2): the developed channel profile vanishes within 0.06 cells of
+    the true plates (halfway bounce-back would leave them at the box faces,
+    0.2-0.3 cells off).  Links at q = 1/2 reproduce halfway bounce-back."""
+    w = channel_wall_fit(orc, 8, 24, 0.125, 0.3, 7.8)
+    assert np.abs(w - [0.3, 7.8]).max() < 0.06
+    w = channel_wall_fit(orc, 8, 24, 0.125, -0.3, 8.25)
+    assert np.abs(w - [-0.3, 8.25]).max() < 0.04
+    halfway = channel_wall_fit(orc, 8, 24, 0.125, 0.3, 7.8, use_q=False)
+    assert np.abs(halfway - [0.0, 8.0]).max() < 1e-3
+    flags = I.nozzle_flags(12, 4, 30)
+    A = orc.Lattice(flags, omega=1.4, u_in=0.01)
+    B = orc.Lattice(flags, omega=1.4, u_in=0.01, wall_q=np.full((flags.size, Q), 128, dtype=np.uint8))
+    for L in (A, B):
+        L.init_equilibrium(1.0, [0.0, 0.0, 0.0])
+        L.step(5)
+    assert np.array_equal(A.f, B.f)
+
+
 def test_plug_flow_is_fixed_point(orc):
     """Uniform flow through a periodic duct with a plug velocity inlet and a
     rho = 1 outlet is an exact steady state of the scheme."""
