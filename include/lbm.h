@@ -167,6 +167,22 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *flags);
 /* Number of active (FLUID + INLET + OUTLET) cells. */
 lbm_status lbm_fluid_count(lbm_ctx *ctx, int64_t *n);
 
+/* Wall distances for Bouzidi's interpolated bounce-back (Sec. 2.2 wall
+ * treatment).  cells[n]: box indices x + nx (y + ny z) of FLUID cells next to
+ * the wall; q[n][27]: for each wall link i of cell r (pull source x - c_i
+ * solid or outside the box), the wall's distance from the cell centre along
+ * the link as q = q[r][i] / 256, 1..255 (128 = halfway, the default of every
+ * link not listed; entries of other links are ignored).  The reflected
+ * population is then interpolated:
+ *   q <  1/2: f_i(x) = 2q f*_ib(x) + (1 - 2q) f*_ib(x + c_i)
+ *             (halfway when x + c_i is solid too),
+ *   q >= 1/2: f_i(x) = f*_ib(x) / (2q) + (1 - 1/(2q)) f*_i(x),
+ * with ib the direction opposite to i.  Copies both arrays to the device;
+ * n = 0 restores halfway bounce-back everywhere; lbm_set_geometry clears
+ * them.  LBM_ERR_ARG for a cell that is not FLUID, a cell listed twice, or
+ * q = 0.  The request server always uses halfway bounce-back. */
+lbm_status lbm_set_wall_q(lbm_ctx *ctx, const int64_t *cells, const uint8_t *q, int64_t n);
+
 /* Set the flow parameters.  omega = 1/(3 nu + 1/2) (Sec. 2.1).
  * Errors: LBM_ERR_ARG unless 0 < omega < 2, ghost rates in (0, 2),
  * |u_in| and u_char below the lattice sound speed 1/sqrt(3). */

@@ -30,6 +30,9 @@ struct lbm_ctx {
     int2 *d_chunks = nullptr;
     int4 *d_bnodes = nullptr;
     int32_t *d_slot_of_active = nullptr;
+    int32_t *d_wall_qidx = nullptr;  // per slot: wall-distance record or -1 (lbm_set_wall_q)
+    uint8_t *d_wall_q = nullptr;     // 32-byte records
+    int64_t n_wall_q = 0;
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
@@ -111,6 +114,14 @@ size_t margin_bytes(const lbm_ctx *c) { return (size_t)buffer_margin(c->desc.nx)
 size_t raw_pop_bytes(const lbm_ctx *c) { return pop_bytes(c) + 2 * margin_bytes(c); }
 size_t raw_mask_bytes(const lbm_ctx *c) { return ((size_t)c->idx.nslots + 2 * MASK_MARGIN) * 4; }
 
+void release_wall_q(lbm_ctx *c) {
+    dev_free(c, c->d_wall_qidx, (size_t)c->idx.nslots * 4);
+    dev_free(c, c->d_wall_q, (size_t)c->n_wall_q * 32);
+    c->d_wall_qidx = nullptr;
+    c->d_wall_q = nullptr;
+    c->n_wall_q = 0;
+}
+
 void release_geometry(lbm_ctx *c) {
     const size_t ns = (size_t)c->idx.nslots;
     dev_free(c, c->f_raw[0], raw_pop_bytes(c));
@@ -120,6 +131,7 @@ void release_geometry(lbm_ctx *c) {
     dev_free(c, c->d_chunks, c->idx.chunks.size() * 8);
     dev_free(c, c->d_bnodes, c->idx.bnodes.size() * 16);
     dev_free(c, c->d_slot_of_active, c->idx.slot_of_active.size() * 4);
+    release_wall_q(c);
     dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     dev_free(c, c->d_health, 8 * 8);
     dev_free(c, c->d_status, 256);
@@ -238,6 +250,8 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
         c->prefetch_key = key;
     }
     a.prefetch_ahead = c->prefetch_ahead;
+    a.wall_qidx = c->d_wall_qidx;
+    a.wall_q = c->d_wall_q;
     a.fin = c->f[c->cur];
     a.fout = c->f[1 - c->cur];
     a.t_new = c->t + 1;
@@ -320,6 +334,48 @@ lbm_status lbm_destroy(lbm_ctx *c) {
 }
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, int64_t n) {
+    lbm_status st = need(c, true, false, false);
+    if (st) return st;
+    if (n < 0 || (n > 0 && (!cells || !q))) return fail(c, LBM_ERR_ARG, "bad wall-distance arrays");
+    DeviceGuard g(c->desc.device);
+    CK(cudaStreamSynchronize(c->stream), "sync before wall distances");
+    release_wall_q(c);
+    if (n == 0) return LBM_OK;
+    const int64_t ncell = (int64_t)c->desc.nx * c->desc.ny * c->desc.nz;
+    // box index -> active index, to find each cell's slot
+    std::vector<int64_t> active_of_box((size_t)ncell, -1);
+    for (int64_t k = 0; k < c->idx.n_active; ++k) active_of_box[(size_t)c->idx.box_of_active[k]] = k;
+    std::vector<int32_t> qidx((size_t)c->idx.nslots, -1);
+    std::vector<uint8_t> rec((size_t)n * 32, 128);
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t b = cells[r];
+        if (b < 0 || b >= ncell || active_of_box[(size_t)b] < 0)
+            return fail(c, LBM_ERR_ARG, "wall-distance record " + std::to_string(r) + " is not an active cell");
+        const int32_t slot = c->idx.slot_of_active[(size_t)active_of_box[(size_t)b]];
+        if (((c->idx.mask[(size_t)slot] >> TYPE_SHIFT) & 3u) != TYPE_FLUID)
+            return fail(c, LBM_ERR_ARG, "wall-distance record " + std::to_string(r) + " is not a fluid cell");
+        if (qidx[(size_t)slot] >= 0)
+            return fail(c, LBM_ERR_ARG, "cell listed twice in the wall distances");
+        for (int i = 0; i < 27; ++i)
+            if (q[r * 27 + i] == 0) return fail(c, LBM_ERR_ARG, "wall distance q = 0 (a wall through a cell centre)");
+        qidx[(size_t)slot] = (int32_t)r;
+        memcpy(&rec[(size_t)r * 32], q + r * 27, 27);
+    }
+    c->d_wall_qidx = (int32_t *)dev_alloc(c, qidx.size() * 4);
+    c->d_wall_q = (uint8_t *)dev_alloc(c, rec.size());
+    c->n_wall_q = n;
+    if (!c->d_wall_qidx || !c->d_wall_q) {
+        release_wall_q(c);
+        return fail(c, LBM_ERR_OOM, "wall-distance allocation failed");
+    }
+    CK(cudaMemcpyAsync(c->d_wall_qidx, qidx.data(), qidx.size() * 4, cudaMemcpyHostToDevice, c->stream),
+       "copy wall index");
+    CK(cudaMemcpyAsync(c->d_wall_q, rec.data(), rec.size(), cudaMemcpyHostToDevice, c->stream), "copy wall records");
+    CK(cudaStreamSynchronize(c->stream), "sync wall distances");
+    return LBM_OK;
+}
 
 lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     if (!c) return LBM_ERR_ARG;

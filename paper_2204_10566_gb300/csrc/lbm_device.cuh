@@ -550,6 +550,46 @@ __device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], in
     }
 }
 
+// Bouzidi's interpolated bounce-back (Sec. 2.2) on the wall links of a cell
+// whose wall distances were given (lbm_set_wall_q).  The gather has already
+// put f*_ib(x) into d[i] for every wall link i (the ghost slot, halfway
+// bounce-back; ib = 26 - i is the direction from x towards the wall), and the
+// pull of ib into d[ib].  With q the wall's distance from x as a fraction of
+// the link:
+//   q <  1/2: f_i = 2q f*_ib(x) + (1 - 2q) f*_ib(x + c_i)   (= d[ib], unless
+//             x + c_i is a wall too: then the halfway value stays),
+//   q >= 1/2: f_i = f*_ib(x) / (2q) + (1 - 1/(2q)) f*_i(x)   (own slot, array i).
+// Every term is a deviation (or scaled deviation) from w_i = w_ib, and the
+// coefficients sum to 1, so the storage form needs no conversion.
+template <int P, bool WIDE, bool RAW>
+__device__ __forceinline__ void interpolate_walls(const StepArgs &a, int slot, uint32_t links,
+                                                  typename Storage<P>::R (&d)[27]) {
+    using S = Storage<P>;
+    using T = typename S::T;
+    using R = typename S::R;
+    const int k = __ldg(a.wall_qidx + slot);
+    if (k < 0) return;
+    const uint8_t *rec = a.wall_q + (size_t)k * 32;
+    const T *fin = static_cast<const T *>(a.fin);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        if (!(links & (1u << i))) continue;
+        const uint32_t q8 = __ldg(rec + i);
+        if (q8 == 128u) continue;
+        const int ib = 26 - i;
+        if (q8 < 128u) {
+            if (links & (1u << ib)) continue;
+            const R q2 = R(q8) * R(1.0 / 128.0);  // 2q
+            d[i] = q2 * d[i] + (R(1) - q2) * d[ib];
+        } else {
+            const T *p = fin + elem<WIDE>(i, a.stride, slot);
+            const R own = RAW ? S::load_raw(p) : S::load(p, R(a.inv_scale));
+            const R c = R(128) / R(q8);  // 1 / (2q)
+            d[i] = c * d[i] + (R(1) - c) * own;
+        }
+    }
+}
+
 // ------------------------------------------------------------------- inlet
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -752,7 +792,7 @@ __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, 
 // there; nothing at inlet/outlet slots).  This completes the 32-byte sectors
 // at the row ends, which the memory system would otherwise have to read
 // back before writing them, at no extra instructions per warp.
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, bool WALLQ = false>
 __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lane, double (&hv)[6]) {
     using R = typename Storage<P>::R;
     const int2 ch = __ldg(a.chunks + chunk);
@@ -770,6 +810,8 @@ __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lan
     R rho, ux, uy, uz;
     constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
     gather<P, WIDE, RAW>(a, nb, x, d);
+    if constexpr (WALLQ)
+        if (links) interpolate_walls<P, WIDE, RAW>(a, slot, links, d);
     if constexpr (GHOST1) {
         const LineStore<P, WIDE, RAW> sink{a, nb, x, slot, links, own};
         collide_ghost1<R, RAW, LineStore<P, WIDE, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
@@ -804,6 +846,11 @@ __device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (
     R d[27];
     R rf, uxf, uyf, uzf, rho, ux, uy, uz;
     gather<P, WIDE>(a, nbf, xf, d);
+    if (a.wall_qidx) {
+        const int sf = nbf[4] + xf;
+        const uint32_t lf = __ldg(a.mask + sf) & LINK_MASK;
+        if (lf) interpolate_walls<P, WIDE, false>(a, sf, lf, d);
+    }
     collide<P, GHOST1>(d, fp, rf, uxf, uyf, uzf, a, slot);  // the node takes its partner's stress
     if (type == TYPE_INLET) {
         R speed = fp.u_in;
@@ -877,12 +924,12 @@ __device__ __forceinline__ void prefetch_block_sources(const StepArgs &a, int tb
 // block also prefetches the pull sources of block blockIdx.x +
 // a.prefetch_ahead into L2 (one bulk prefetch per population), so that the
 // gathers of later blocks find their rows in L2 instead of waiting on HBM.
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, bool WALLQ>
 __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
     const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
     const int chunk = gt / CHUNK;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE>(a, chunk, gt % CHUNK, hv);
+    if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE, WALLQ>(a, chunk, gt % CHUNK, hv);
     if (a.prefetch_ahead > 0) {
         const int i = (int)threadIdx.x - (STEP_THREADS - 32);
         if (i >= 0 && i < 27) prefetch_block_sources<P>(a, (int)blockIdx.x + a.prefetch_ahead, i);
@@ -1082,10 +1129,12 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
     int per_sm = 0, sms = 0;
     cudaError_t e;
     if (ghost1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, true, true> : k_step<P, true, false>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, true, true, false>
+                                                                        : k_step<P, true, false, false>,
                                                           STEP_THREADS, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, false, true> : k_step<P, false, false>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, false, true, false>
+                                                                        : k_step<P, false, false, false>,
                                                           STEP_THREADS, 0);
     if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
@@ -1097,7 +1146,10 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
 
 template <int P, bool G, bool WD>
 void launch_fluid(const StepArgs &a, cudaStream_t s) {
-    k_step<P, G, WD><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
+    if (a.wall_qidx)  // interpolated bounce-back on the listed wall links
+        k_step<P, G, WD, true><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
+    else
+        k_step<P, G, WD, false><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
 }
 
 template <int P>

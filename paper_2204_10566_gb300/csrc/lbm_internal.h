@@ -100,6 +100,8 @@ struct alignas(16) StepArgs {
     double *partials;       // [gridDim.x][REDUCE_SLOTS]
     int32_t prefetch_ahead; // fluid blocks between a block and the one whose sources it prefetches to L2 (0: off)
     int32_t inlet_ramp;     // steps over which the inlet velocity rises from 0 (0: impulsive start)
+    const int32_t *wall_qidx;  // per slot: wall-distance record of the cell, or -1 (NULL: q = 1/2 everywhere)
+    const uint8_t *wall_q;     // records of 32 bytes: q = k / 256 of wall link i in byte i
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).

@@ -1,7 +1,7 @@
 // Request server: continuous batching of many lattices on one GPU.
 //
 // Requests (flag field, flow parameters, step count, storage precision) are
-// queued by lbm_server_submit; a host worker thread builds each request's
+// queued by lbm_server_submit; host worker threads build each request's
 // sparse index while the GPU is busy.  lbm_server_tick admits ready requests
 // into resident slots by exact device footprint against the budget, then
 // advances every resident lattice by up to steps_per_tick steps with one
@@ -126,7 +126,7 @@ struct Request {
     int state = LBM_REQ_QUEUED;
     int64_t steps_done = 0;
     bool cancel = false;
-    // built by the worker thread (guarded by the server mutex)
+    // built by a worker thread (guarded by the server mutex)
     bool index_ready = false;
     std::string index_error;
     HostIndex idx;
@@ -154,8 +154,8 @@ struct lbm_server {
     int64_t next_id = 1;
     int64_t in_use = 0, peak = 0;
     double cell_updates = 0, ticks = 0, graph_launches = 0, graph_captures = 0, finished = 0;
-    // worker thread building indexes
-    std::thread worker;
+    // worker threads building indexes
+    std::vector<std::thread> workers;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request *> build_queue;
@@ -311,7 +311,11 @@ lbm_status lbm_server_create(const lbm_server_desc *desc, lbm_server **out) {
     occupancy_grids<1>(sms, s->grid_fluid[0], s->grid_bnd[0]);
     occupancy_grids<2>(sms, s->grid_fluid[1], s->grid_bnd[1]);
     lbm_server *raw = s.get();
-    s->worker = std::thread(worker_loop, raw);
+    // Index building is host work that is independent per request: a few
+    // threads keep admission fed when many small requests arrive at once.
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nworkers = (int)std::max(1u, std::min(4u, hw > 1 ? hw - 1 : 1u));
+    for (int k = 0; k < nworkers; ++k) s->workers.emplace_back(worker_loop, raw);
     *out = s.release();
     return LBM_OK;
 }
@@ -323,7 +327,8 @@ lbm_status lbm_server_destroy(lbm_server *s) {
         s->stop = true;
     }
     s->cv.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    for (auto &w : s->workers)
+        if (w.joinable()) w.join();
     cudaSetDevice(s->desc.device);
     cudaStreamSynchronize(s->stream);
     for (auto &kv : s->reqs) release(s, kv.second.get());

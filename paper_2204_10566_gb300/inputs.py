@@ -60,6 +60,66 @@ def nozzle_flags(D, d, L_total, L_in=None, L_cone=None, L_throat=None, half_angl
     return flags
 
 
+def nozzle_radius_array(z, D, d, L_in, L_cone, L_throat, half_angle_deg=10.0):
+    """nozzle_radius for an array of axial positions."""
+    z = np.asarray(z, dtype=np.float64)
+    t = math.tan(math.radians(half_angle_deg))
+    cone = np.maximum(D / 2.0 - (z - L_in) * t, d / 2.0)
+    r = np.where(z < L_in, D / 2.0, np.where(z < L_in + L_cone, cone,
+                                              np.where(z < L_in + L_cone + L_throat, d / 2.0, D / 2.0)))
+    return r
+
+
+def nozzle_wall_q(D, d, L_total, L_in=None, L_cone=None, L_throat=None, half_angle_deg=10.0, flags=None,
+                  iterations=40):
+    """Wall distances of the smooth nozzle surface for the interpolated
+    bounce-back: for every FLUID cell of the voxelised nozzle and every link i
+    whose pull source x - c_i is solid (or outside the box), the fraction q of
+    the link, from the cell centre towards x - c_i, at which the segment
+    first leaves the nozzle (bisection on the signed radius distance).
+    Returns (cells, q): box indices (n,) and q quantised to uint8 in 1/256
+    (1..255) as an (n, 27) array, 128 on the other links."""
+    L_in = D if L_in is None else L_in
+    L_cone = cone_length(D, d, half_angle_deg) if L_cone is None else L_cone
+    L_throat = 4 * d if L_throat is None else L_throat
+    if flags is None:
+        flags = nozzle_flags(D, d, L_total, L_in, L_cone, L_throat, half_angle_deg)
+    nz, ny, nx = flags.shape
+    c = np.array([[i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1] for i in range(27)])
+    fz, fy, fx = np.nonzero(flags == FLUID)
+    solid_src = np.zeros((fz.size, 27), dtype=bool)
+    for i in range(27):
+        sx, sy, sz = fx - c[i, 0], fy - c[i, 1], fz - c[i, 2]
+        inside = (sx >= 0) & (sx < nx) & (sy >= 0) & (sy < ny) & (sz >= 0) & (sz < nz)
+        fl = np.zeros(fz.size, dtype=np.uint8)
+        fl[inside] = flags[sz[inside], sy[inside], sx[inside]]
+        solid_src[:, i] = fl == SOLID
+    rows = np.nonzero(solid_src.any(axis=1))[0]
+    q = np.full((rows.size, 27), 128, dtype=np.uint8)
+    px, py, pz = fx[rows] + 0.5, fy[rows] + 0.5, fz[rows] + 0.5
+
+    def outside(s, i):  # point at fraction s of link i from the cell centre
+        x, y, z = px - s * c[i, 0], py - s * c[i, 1], pz - s * c[i, 2]
+        r = np.hypot(x - D / 2.0, y - D / 2.0)
+        return r > nozzle_radius_array(z, D, d, L_in, L_cone, L_throat, half_angle_deg)
+
+    for i in range(27):
+        sel = solid_src[rows, i]
+        if not sel.any():
+            continue
+        lo = np.zeros(rows.size)
+        hi = np.ones(rows.size)
+        for _ in range(iterations):
+            mid = 0.5 * (lo + hi)
+            out = outside(mid, i)
+            hi = np.where(out, mid, hi)
+            lo = np.where(out, lo, mid)
+        k = np.clip(np.rint(hi * 256.0), 1, 255).astype(np.uint8)
+        q[sel, i] = k[sel]
+    cells = (fx[rows].astype(np.int64) + nx * (fy[rows].astype(np.int64) + ny * fz[rows].astype(np.int64)))
+    return cells, q
+
+
 def pipe_flags(D, L_total, inlet=True, outlet=True):
     """Straight circular pipe of diameter D (cells) along z."""
     return nozzle_flags(D, D, L_total, L_in=L_total, L_cone=1, L_throat=0, inlet=inlet, outlet=outlet)

@@ -99,6 +99,7 @@ _SIGS = {
                                    C.POINTER(C.c_int64)]),
     "lbm_set_geometry": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_fluid_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "lbm_set_wall_q": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "lbm_set_params": (C.c_int, [C.c_void_p, C.POINTER(lbm_params)]),
     "lbm_get_omega": (C.c_int, [C.c_void_p, _dp]),
     "lbm_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, _dp]),
@@ -297,6 +298,17 @@ class Lattice:
         return self.n_active if layout == LBM_LAYOUT_ACTIVE else int(np.prod(self.shape))
 
     # -- parameters and state
+    def set_wall_q(self, cells, q):
+        """lbm_set_wall_q: cells (n,) box indices, q (n, 27) uint8 wall
+        distances in 1/256 of a link (128 = halfway); empty clears them."""
+        cells = np.ascontiguousarray(cells, dtype=np.int64).reshape(-1)
+        q = np.ascontiguousarray(q, dtype=np.uint8).reshape(-1, 27)
+        if q.shape[0] != cells.size:
+            raise ValueError("cells and q disagree in length")
+        self._check(self.lib.lbm_set_wall_q(self.ctx, cells.ctypes.data if cells.size else None,
+                                            q.ctypes.data if cells.size else None, cells.size))
+        return self
+
     def set_params(self, **kw):
         """lbm_set_params; keywords as make_params."""
         p = make_params(**kw)

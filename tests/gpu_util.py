@@ -14,12 +14,12 @@ def omega_of_nu(nu):
 
 
 def oracle_lattice(orc, flags, nu, periodic=0, ghost=(1.0, 1.0, 1.0, 1.0), profile="plug", u_in=0.0, d_in=None,
-                   noise_amp=0.0, seed=0, rho_out=1.0, ramp=0):
+                   noise_amp=0.0, seed=0, rho_out=1.0, ramp=0, wall_q=None):
     nz, ny, nx = flags.shape
     return orc.Lattice(flags, omega_of_nu(nu), ghost=ghost, periodic=periodic,
                        profile=orc.PLUG if profile == "plug" else orc.PARABOLIC, u_in=u_in,
                        d_in=d_in if d_in else nx, axis=(nx / 2.0, ny / 2.0), noise_amp=noise_amp, seed=seed,
-                       rho_out=rho_out, ramp=ramp)
+                       rho_out=rho_out, ramp=ramp, wall_q=wall_q)
 
 
 def gpu_lattice(lbm, flags, precision, nu, periodic=0, ghost=(1.0, 1.0, 1.0, 1.0), profile="plug", u_in=0.0,
