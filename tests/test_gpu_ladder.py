@@ -1,0 +1,102 @@
+"""Grid convergence and collision stability (GPU required).
+
+Resolution ladder (the paper's R1-R3 study, Sec. 3): the Re 3500 nozzle at
+throat diameters d = 18, 24 and 36 cells (the paper's spacing ratios
+1 : 1.33 : 2), walls interpolated on the smooth surface as in the paper, the
+same throat velocity 0.05 (acoustic scaling: steps grow with d) and the same
+smooth inlet start in throat flow-through units.  The time-averaged
+centreline velocity upstream of the sudden expansion, as a function of
+z / d, converges monotonically: measured 6.9 % (R1) and 3.5 % (R2) from R3,
+the ratio of first-order convergence, the differences sitting in the throat
+(the paper reports ~3 % between its levels there).  With voxelised
+(halfway) walls the coarsest level diverges.
+
+Ghost rates (Appendix A): relaxing every moment of order 3-6 to equilibrium
+(rate 1, the paper's choice) keeps an under-resolved Taylor-Green vortex
+stable where relaxing them at omega (lattice BGK with the same full Hermite
+equilibrium) diverges.
+"""
+import numpy as np
+import pytest
+
+from paper_2204_10566_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BOX = 1
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2204_10566_gb300 import build
+
+    build.build()
+    from paper_2204_10566_gb300 import lbm as m
+
+    assert torch.cuda.is_available()
+    return m
+
+
+def ladder_level(lbm, d, smooth, flow_units=30.0, u=0.05, Re=3500.0):
+    D, L = 3 * d, 25 * d
+    flags = I.nozzle_flags(D, d, L)
+    steps = int(flow_units * d / u)
+    G = lbm.Lattice(flags, "fp32")
+    G.set_params(Re=Re, u_char=u, L_char=float(d), u_in=u * (d / D) ** 2, d_in=float(D), profile="parabolic",
+                 noise_amp=0.0, inlet_ramp=steps * 2 // 5)
+    if smooth:
+        G.set_wall_q(*I.nozzle_wall_q(D, d, L, flags=flags))
+    G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
+    G.step(steps // 2)
+    G.stats_begin(1)
+    G.step(steps - steps // 2).sync()
+    m1, _, _ = G.stats_get(BOX)
+    G.close()
+    line = m1.reshape(L, D, D)[:, D // 2, D // 2]
+    z = (np.arange(L) + 0.5) / d
+    return z, line / u, (D + I.cone_length(D, d) + 4 * d) / d
+
+
+def test_resolution_ladder_converges(lbm):
+    smooth = True
+    levels = [ladder_level(lbm, d, smooth) for d in (18, 24, 36)]
+    z_exp = min(lv[2] for lv in levels)
+    zq = np.linspace(0.5, z_exp - 0.5, 200)
+    prof = [np.interp(zq, z, u) for z, u, _ in levels]
+    e1 = np.linalg.norm(prof[0] - prof[2]) / np.linalg.norm(prof[2])
+    e2 = np.linalg.norm(prof[1] - prof[2]) / np.linalg.norm(prof[2])
+    print("ladder smooth=%s: finite %s |R1-R3| %.4g  |R2-R3| %.4g" % (smooth, [bool(np.isfinite(p).all()) for p in prof], e1, e2))
+    for zz in (1.0, 3.0, 6.0, 9.0, 12.0, z_exp - 1):
+        print("  z/d %.1f: %s" % (zz, [round(float(np.interp(zz, zq, p)), 4) for p in prof]))
+    assert np.isfinite(prof).all()
+    assert e2 < e1 and 1.5 < e1 / e2 < 4.0  # monotone, between first and second order
+    assert e2 < 0.05
+
+
+def tgv_energy(lbm, n, Re, ghost, steps, u0=0.05):
+    nu = u0 * n / (2 * np.pi) / Re
+    k = 2 * np.pi / n
+    c = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    u = np.stack([u0 * np.sin(k * X) * np.cos(k * Y) * np.cos(k * Z),
+                  -u0 * np.cos(k * X) * np.sin(k * Y) * np.cos(k * Z), np.zeros_like(X)], axis=-1)
+    G = lbm.Lattice(np.ones((n, n, n), dtype=np.uint8), "fp32", periodic=7)
+    omega = 1.0 / (3.0 * nu + 0.5)
+    G.set_params(nu=nu, ghost=ghost if ghost is not None else (omega,) * 4)
+    G.init_fields(np.ones(n ** 3), u.reshape(-1, 3), layout=BOX)
+    G.step(steps).sync()
+    e = float((G.moments(BOX)[1] ** 2).sum()) / n ** 3
+    G.close()
+    return e
+
+
+def test_unit_ghost_rates_stabilise_under_resolved_flow(lbm):
+    n, steps = 64, 4000
+    e0 = 0.05 ** 2 / 4  # mean u^2 of the initial field
+    for Re in (1600.0, 20000.0, 200000.0):
+        e_chm = tgv_energy(lbm, n, Re, (1.0, 1.0, 1.0, 1.0), steps)
+        e_bgk = tgv_energy(lbm, n, Re, None, steps)
+        print("TGV 64^3 Re %g: energy CHM ghost 1 %.4g, all rates omega %.4g" % (Re, e_chm, e_bgk))
+        assert np.isfinite(e_chm) and 0.0 < e_chm < e0
+    assert not (np.isfinite(e_bgk) and e_bgk < e0)  # all rates omega: diverged at Re 200 000
