@@ -33,6 +33,9 @@ struct lbm_ctx {
     int32_t *d_wall_qidx = nullptr;  // per slot: wall-distance record or -1 (lbm_set_wall_q)
     uint8_t *d_wall_q = nullptr;     // 32-byte records
     int64_t n_wall_q = 0;
+    int4 *d_wnodes = nullptr;        // cells with interpolated walls, out of the chunk lanes
+    int64_t n_wnodes = 0;
+    int2 *d_chunks_wall = nullptr;   // chunk records without those cells (the fluid kernel's list)
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
@@ -117,9 +120,14 @@ size_t raw_mask_bytes(const lbm_ctx *c) { return ((size_t)c->idx.nslots + 2 * MA
 void release_wall_q(lbm_ctx *c) {
     dev_free(c, c->d_wall_qidx, (size_t)c->idx.nslots * 4);
     dev_free(c, c->d_wall_q, (size_t)c->n_wall_q * 32);
+    dev_free(c, c->d_wnodes, (size_t)c->n_wnodes * 16);
+    if (c->d_chunks_wall) dev_free(c, c->d_chunks_wall, c->idx.chunks.size() * 8);
+    c->d_chunks_wall = nullptr;
     c->d_wall_qidx = nullptr;
     c->d_wall_q = nullptr;
+    c->d_wnodes = nullptr;
     c->n_wall_q = 0;
+    c->n_wnodes = 0;
 }
 
 void release_geometry(lbm_ctx *c) {
@@ -207,7 +215,7 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     StepArgs a{};
     a.mask = c->d_mask;
     a.row_nb = c->d_row_nb;
-    a.chunks = c->d_chunks;
+    a.chunks = c->d_chunks_wall ? c->d_chunks_wall : c->d_chunks;
     a.stride = c->idx.nslots;
     a.nchunks = (int32_t)c->idx.chunks.size();
     a.bnodes = c->d_bnodes;
@@ -252,6 +260,8 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.prefetch_ahead = c->prefetch_ahead;
     a.wall_qidx = c->d_wall_qidx;
     a.wall_q = c->d_wall_q;
+    a.wnodes = c->d_wnodes;
+    a.nwnodes = (int32_t)c->n_wnodes;
     a.fin = c->f[c->cur];
     a.fout = c->f[1 - c->cur];
     a.t_new = c->t + 1;
@@ -342,6 +352,7 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     DeviceGuard g(c->desc.device);
     CK(cudaStreamSynchronize(c->stream), "sync before wall distances");
     release_wall_q(c);
+    c->step_blocks = c->fluid_blocks + node_blocks((int64_t)c->idx.bnodes.size());  // no wall kernel
     if (n == 0) return LBM_OK;
     const int64_t ncell = (int64_t)c->desc.nx * c->desc.ny * c->desc.nz;
     // box index -> active index, to find each cell's slot
@@ -363,16 +374,63 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
         qidx[(size_t)slot] = (int32_t)r;
         memcpy(&rec[(size_t)r * 32], q + r * 27, 27);
     }
+    // cells with at least one interpolated link leave the chunk lanes for the
+    // wall kernel's list (slot order)
+    const int ny_e = c->idx.ny_e;
+    std::vector<int4> wn;
+    std::vector<int2> chunks = c->idx.chunks;
+    std::vector<char> is_wall((size_t)c->idx.nslots, 0);
+    for (int64_t r = 0; r < n; ++r) {
+        bool interp = false;
+        for (int i = 0; i < 27; ++i) interp |= q[r * 27 + i] != 128;
+        if (!interp) continue;
+        const int64_t b = cells[r];
+        const int x = (int)(b % c->desc.nx), y = (int)((b / c->desc.nx) % c->desc.ny);
+        const int z = (int)(b / ((int64_t)c->desc.nx * c->desc.ny));
+        const int row = (y + 1) + ny_e * (z + 1);
+        const int32_t slot = c->idx.slot_of_active[(size_t)active_of_box[(size_t)b]];
+        wn.push_back(make_int4(x, row, slot, (int)r));
+        is_wall[(size_t)slot] = 1;
+    }
+    std::sort(wn.begin(), wn.end(), [](const int4 &p, const int4 &q2) { return p.z < q2.z; });
+    for (int2 &ch : chunks) {
+        const int x0 = (int)((uint32_t)ch.y & CHUNK_X0_MASK);
+        const int32_t base = c->idx.row_nb[(size_t)ch.x * ROW_RECORD_INTS + 4];
+        uint32_t lanes = ((uint32_t)ch.y >> CHUNK_LANES_SHIFT) & 0xFFu;
+        for (int l = 0; l < CHUNK; ++l)
+            if (((lanes >> l) & 1u) && is_wall[(size_t)(base + x0 + l)]) lanes &= ~(1u << l);
+        ch.y = (int)((uint32_t)x0 | (lanes << CHUNK_LANES_SHIFT));
+    }
     c->d_wall_qidx = (int32_t *)dev_alloc(c, qidx.size() * 4);
     c->d_wall_q = (uint8_t *)dev_alloc(c, rec.size());
     c->n_wall_q = n;
-    if (!c->d_wall_qidx || !c->d_wall_q) {
+    c->n_wnodes = (int64_t)wn.size();
+    c->d_wnodes = wn.empty() ? nullptr : (int4 *)dev_alloc(c, wn.size() * 16);
+    if (!wn.empty()) c->d_chunks_wall = (int2 *)dev_alloc(c, chunks.size() * 8);
+    const int step_blocks = c->fluid_blocks + node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(c->n_wnodes);
+    double *partials = c->d_partials;
+    if (step_blocks > c->nblocks) {  // room for the wall kernel's partial sums
+        partials = (double *)dev_alloc(c, (size_t)step_blocks * REDUCE_SLOTS * 8);
+        if (partials) {
+            dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
+            c->d_partials = partials;
+            c->nblocks = step_blocks;
+        }
+    }
+    if (!c->d_wall_qidx || !c->d_wall_q || (!wn.empty() && (!c->d_wnodes || !c->d_chunks_wall)) || !partials) {
         release_wall_q(c);
         return fail(c, LBM_ERR_OOM, "wall-distance allocation failed");
     }
     CK(cudaMemcpyAsync(c->d_wall_qidx, qidx.data(), qidx.size() * 4, cudaMemcpyHostToDevice, c->stream),
        "copy wall index");
     CK(cudaMemcpyAsync(c->d_wall_q, rec.data(), rec.size(), cudaMemcpyHostToDevice, c->stream), "copy wall records");
+    if (!wn.empty())
+        CK(cudaMemcpyAsync(c->d_wnodes, wn.data(), wn.size() * 16, cudaMemcpyHostToDevice, c->stream),
+           "copy wall cells");
+    if (!wn.empty())
+        CK(cudaMemcpyAsync(c->d_chunks_wall, chunks.data(), chunks.size() * 8, cudaMemcpyHostToDevice, c->stream),
+           "copy chunk lanes");
+    c->step_blocks = step_blocks;
     CK(cudaStreamSynchronize(c->stream), "sync wall distances");
     return LBM_OK;
 }

@@ -34,6 +34,11 @@
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 8
 #endif
+// The same for the kernel of the cells with interpolated walls, which keeps
+// the wall record and the own-slot values of a cell in registers as well.
+#ifndef LBM_STEP_MIN_BLOCKS_WALLQ
+#define LBM_STEP_MIN_BLOCKS_WALLQ 4
+#endif
 // L2 prefetch lookahead of the fluid kernel, in percent of the blocks
 // resident on the device (0 disables the prefetch).  At 8 blocks per SM the
 // FP32 kernel keeps enough loads in flight on its own (the prefetch measured
@@ -564,30 +569,40 @@ __device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], in
 // Every term is a deviation (or scaled deviation) from w_i = w_ib, and the
 // coefficients sum to 1, so the storage form needs no conversion.
 template <int P, bool WIDE, bool RAW>
-__device__ __forceinline__ void interpolate_walls(const StepArgs &a, int slot, uint32_t links,
+__device__ __forceinline__ void interpolate_walls(const StepArgs &a, int k, int slot, uint32_t links,
                                                   typename Storage<P>::R (&d)[27]) {
     using S = Storage<P>;
     using T = typename S::T;
     using R = typename S::R;
-    const int k = __ldg(a.wall_qidx + slot);
     if (k < 0) return;
-    const uint8_t *rec = a.wall_q + (size_t)k * 32;
+    // the record as two 16-byte loads; byte i = q of link i in 1/256
+    const uint4 *rec = reinterpret_cast<const uint4 *>(a.wall_q) + 2 * (size_t)k;
+    const uint4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+    const uint32_t w[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
     const T *fin = static_cast<const T *>(a.fin);
+    // own-slot values for the links with q > 1/2, all loads issued first
+    R own[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const uint32_t q8 = (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+        own[i] = R(0);
+        if ((links & (1u << i)) && q8 > 128u) {
+            const T *p = fin + elem<WIDE>(i, a.stride, slot);
+            own[i] = RAW ? S::load_raw(p) : S::load(p, R(a.inv_scale));
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         if (!(links & (1u << i))) continue;
-        const uint32_t q8 = __ldg(rec + i);
-        if (q8 == 128u) continue;
+        const uint32_t q8 = (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
         const int ib = 26 - i;
         if (q8 < 128u) {
             if (links & (1u << ib)) continue;
             const R q2 = R(q8) * R(1.0 / 128.0);  // 2q
             d[i] = q2 * d[i] + (R(1) - q2) * d[ib];
-        } else {
-            const T *p = fin + elem<WIDE>(i, a.stride, slot);
-            const R own = RAW ? S::load_raw(p) : S::load(p, R(a.inv_scale));
+        } else if (q8 > 128u) {
             const R c = R(128) / R(q8);  // 1 / (2q)
-            d[i] = c * d[i] + (R(1) - c) * own;
+            d[i] = c * d[i] + (R(1) - c) * own[i];
         }
     }
 }
@@ -794,15 +809,11 @@ __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, 
 // there; nothing at inlet/outlet slots).  This completes the 32-byte sectors
 // at the row ends, which the memory system would otherwise have to read
 // back before writing them, at no extra instructions per warp.
-template <int P, bool GHOST1, bool WIDE, bool WALLQ = false>
-__device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lane, double (&hv)[6]) {
+template <int P, bool GHOST1, bool WIDE, bool WALLQ>
+__device__ __forceinline__ void cell_update(const StepArgs &a, int row, int x, bool fluid, int qk, double (&hv)[6]) {
     using R = typename Storage<P>::R;
-    const int2 ch = __ldg(a.chunks + chunk);
-    const uint32_t cw = (uint32_t)ch.y;
-    const bool fluid = (cw >> (CHUNK_LANES_SHIFT + lane)) & 1u;
-    const int x = (int)(cw & CHUNK_X0_MASK) + lane;
     int nb[9];
-    load_row(a.row_nb, ch.x, nb);
+    load_row(a.row_nb, row, nb);
     const int slot = nb[4] + x;
     const uint32_t m = __ldg(a.mask + slot);  // needed after the collision only
     const uint32_t links = fluid ? (m & LINK_MASK) : 0u;
@@ -812,8 +823,7 @@ __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lan
     R rho, ux, uy, uz;
     constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
     gather<P, WIDE, RAW>(a, nb, x, d);
-    if constexpr (WALLQ)
-        if (links) interpolate_walls<P, WIDE, RAW>(a, slot, links, d);
+    if constexpr (WALLQ) interpolate_walls<P, WIDE, RAW>(a, qk, slot, links, d);
     if constexpr (GHOST1) {
         const LineStore<P, WIDE, RAW> sink{a, nb, x, slot, links, own};
         collide_ghost1<R, RAW, LineStore<P, WIDE, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
@@ -824,6 +834,24 @@ __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lan
         store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
     }
     if (fluid) record_cell(a, slot, rho, ux, uy, uz, hv);
+}
+
+template <int P, bool GHOST1, bool WIDE>
+__device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lane, double (&hv)[6]) {
+    const int2 ch = __ldg(a.chunks + chunk);
+    const uint32_t cw = (uint32_t)ch.y;
+    const bool fluid = (cw >> (CHUNK_LANES_SHIFT + lane)) & 1u;
+    cell_update<P, GHOST1, WIDE, false>(a, ch.x, (int)(cw & CHUNK_X0_MASK) + lane, fluid, -1, hv);
+}
+
+// Update of wall cell k of the interpolated-wall list (x, row, slot, record):
+// the same update with Bouzidi's interpolation of its wall links.  These
+// cells are taken out of the chunk lanes while wall distances are set, so
+// the fluid kernel keeps its plain instruction stream.
+template <int P, bool GHOST1, bool WIDE>
+__device__ __forceinline__ void wall_cell(const StepArgs &a, int k, double (&hv)[6]) {
+    const int4 node = __ldg(a.wnodes + k);
+    cell_update<P, GHOST1, WIDE, true>(a, node.y, node.x, true, node.w, hv);
 }
 
 // Update of inlet/outlet node k: non-equilibrium extrapolation (Sec. 2.2)
@@ -851,7 +879,7 @@ __device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (
     if (a.wall_qidx) {
         const int sf = nbf[4] + xf;
         const uint32_t lf = __ldg(a.mask + sf) & LINK_MASK;
-        if (lf) interpolate_walls<P, WIDE, false>(a, sf, lf, d);
+        if (lf) interpolate_walls<P, WIDE, false>(a, __ldg(a.wall_qidx + sf), sf, lf, d);
     }
     collide<P, GHOST1>(d, fp, rf, uxf, uyf, uzf, a, slot);  // the node takes its partner's stress
     if (type == TYPE_INLET) {
@@ -926,12 +954,12 @@ __device__ __forceinline__ void prefetch_block_sources(const StepArgs &a, int tb
 // block also prefetches the pull sources of block blockIdx.x +
 // a.prefetch_ahead into L2 (one bulk prefetch per population), so that the
 // gathers of later blocks find their rows in L2 instead of waiting on HBM.
-template <int P, bool GHOST1, bool WIDE, bool WALLQ>
+template <int P, bool GHOST1, bool WIDE>
 __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
     const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
     const int chunk = gt / CHUNK;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE, WALLQ>(a, chunk, gt % CHUNK, hv);
+    if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE>(a, chunk, gt % CHUNK, hv);
     if (a.prefetch_ahead > 0) {
         const int i = (int)threadIdx.x - (STEP_THREADS - 32);
         if (i >= 0 && i < 27) prefetch_block_sources<P>(a, (int)blockIdx.x + a.prefetch_ahead, i);
@@ -940,6 +968,19 @@ __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS
 }
 
 // One time step of every inlet/outlet node of one lattice.
+// One time step of the cells with interpolated walls (see wall_cell); its
+// partial sums follow those of the fluid and inlet/outlet kernels.
+template <int P, bool GHOST1, bool WIDE>
+__global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS_WALLQ) k_wall(const StepArgs a) {
+    const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
+    double hv[6] = {0, 0, 0, 0, 0, 0};
+    if (k < a.nwnodes) wall_cell<P, GHOST1, WIDE>(a, k, hv);
+    if (a.flags & STEP_REDUCE) {
+        const int before = a.fluid_blocks + (a.nbnodes + STEP_THREADS - 1) / STEP_THREADS;
+        block_reduce_write(hv, a.partials + (size_t)before * REDUCE_SLOTS);
+    }
+}
+
 template <int P, bool GHOST1, bool WIDE>
 __global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
     const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
@@ -1131,12 +1172,10 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
     int per_sm = 0, sms = 0;
     cudaError_t e;
     if (ghost1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, true, true, false>
-                                                                        : k_step<P, true, false, false>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, true, true> : k_step<P, true, false>,
                                                           STEP_THREADS, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, false, true, false>
-                                                                        : k_step<P, false, false, false>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, false, true> : k_step<P, false, false>,
                                                           STEP_THREADS, 0);
     if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
@@ -1148,10 +1187,9 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
 
 template <int P, bool G, bool WD>
 void launch_fluid(const StepArgs &a, cudaStream_t s) {
-    if (a.wall_qidx)  // interpolated bounce-back on the listed wall links
-        k_step<P, G, WD, true><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
-    else
-        k_step<P, G, WD, false><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
+    k_step<P, G, WD><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
+    if (a.nwnodes > 0)  // cells with interpolated walls
+        k_wall<P, G, WD><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
 }
 
 template <int P>

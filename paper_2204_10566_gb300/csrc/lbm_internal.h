@@ -102,6 +102,9 @@ struct alignas(16) StepArgs {
     int32_t inlet_ramp;     // steps over which the inlet velocity rises from 0 (0: impulsive start)
     const int32_t *wall_qidx;  // per slot: wall-distance record of the cell, or -1 (NULL: q = 1/2 everywhere)
     const uint8_t *wall_q;     // records of 32 bytes: q = k / 256 of wall link i in byte i
+    const int4 *wnodes;        // cells with interpolated walls (x, row, slot, record), out of the chunk lanes
+    int32_t nwnodes;
+    int32_t reserved2_;
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).

@@ -137,3 +137,28 @@ def test_round_pipe_closer_to_hagen_poiseuille(lbm):
     e_q = pipe_shape_error(lbm, 16, True)
     print("pipe shape error: halfway %.4g, interpolated %.4g" % (e_stair, e_q))
     assert e_q < 0.5 * e_stair
+
+
+def test_wall_cells_enter_health_and_statistics(lbm):
+    """The cells with interpolated walls run in their own kernel; the fused
+    health check and the statistics still cover every active cell."""
+    D, d, L = 12, 4, 40
+    flags = I.nozzle_flags(D, d, L)
+    cells, q = I.nozzle_wall_q(D, d, L)
+    G = gpu_lattice(lbm, flags, "fp64", 0.02, profile="parabolic", u_in=0.01, d_in=float(D))
+    G.set_wall_q(cells, q)
+    G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
+    G.step(60)
+    G.set_check_every(2)
+    G.stats_begin(1)
+    acc = np.zeros(G.n_active)
+    for _ in range(6):
+        G.step(1)
+        acc += G.moments()[1][:, 2]
+    G.sync()
+    h = G.health()
+    rho, u = G.moments()
+    assert abs(h[0] - rho.sum()) < 1e-10 * rho.sum()
+    assert np.abs(h[1:4] - (rho[:, None] * u).sum(axis=0)).max() < 1e-12 * rho.sum()
+    m1, _, n = G.stats_get()
+    assert n == 6 and np.abs(m1 - acc / 6).max() < 1e-15
