@@ -121,6 +121,9 @@ void lbm_params_default(lbm_params *p);
 
 /* Create a context on desc->device bound to desc->stream.  Allocates nothing
  * on the device until lbm_set_geometry.  *out receives the context.
+ * Lattices of 2^32 / 27 slots or more step with 64-bit element offsets; with
+ * the environment variable LBM_WIDE_OFFSETS=1 at creation, every lattice
+ * does (for testing that path on small lattices).
  * Errors: LBM_ERR_ARG (bad sizes, precision, scale), LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out);
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -36,6 +37,7 @@ struct lbm_ctx {
     int4 *d_wnodes = nullptr;        // cells with interpolated walls, out of the chunk lanes
     int64_t n_wnodes = 0;
     int2 *d_chunks_wall = nullptr;   // chunk records without those cells (the fluid kernel's list)
+    bool wide_offsets = false;       // LBM_WIDE_OFFSETS=1 at creation: the 64-bit offset kernels always
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
@@ -251,7 +253,8 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.inv_scale = 1.0f / a.scale;
     a.stats = c->d_stats;
     a.partials = c->d_partials;
-    const bool wide = a.stride > MAX_SLOTS_32;
+    a.wide_offsets = c->wide_offsets ? 1 : 0;
+    const bool wide = a.wide_offsets || a.stride > MAX_SLOTS_32;
     const int key = (c->ghost1 ? 2 : 0) + (wide ? 1 : 0);
     if (c->prefetch_key != key) {
         c->prefetch_ahead = DISPATCH(c->desc.precision, step_prefetch_ahead, c->ghost1, wide, c->desc.device);
@@ -329,6 +332,11 @@ lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out) {
     c->desc = *desc;
     c->desc.fp16_scale = s;
     c->stream = static_cast<cudaStream_t>(desc->stream);
+    // Lattices of 2^32 / 27 slots or more need 64-bit element offsets; this
+    // switch runs those kernels on any lattice, so that tests can cover them
+    // without allocating tens of gigabytes.
+    const char *wide = std::getenv("LBM_WIDE_OFFSETS");
+    c->wide_offsets = wide && wide[0] == '1';
     lbm_params_default(&c->params);
     *out = c;
     return LBM_OK;

@@ -88,7 +88,11 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                 }
             }
     std::vector<int32_t> base((size_t)nrows, 0);
-    int64_t next = 0;
+    // Storage starts nx + 8 slots in: every chunk lane (fluid or not) then pulls
+    // from a non-negative slot, so the 32-bit unsigned element offsets of the
+    // step kernel never wrap (a non-fluid lane may pull from before the first
+    // stored cell of a neighbour row).
+    int64_t next = ((int64_t)nx + 8 + CHUNK - 1) / CHUNK * CHUNK;
     for (int64_t r = 0; r < nrows; ++r) {
         if (need_lo[r] == INT_MAX) continue;
         const int lo = (int)std::floor(need_lo[r] / (double)CHUNK) * CHUNK;
@@ -235,7 +239,8 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     for (int64_t b = 0; b < (int64_t)seen.size(); ++b)
         if ((flags[b] == LBM_FLUID) != (seen[b] == 1)) return "fluid cell not in exactly one chunk lane";
     // every lane of every chunk (fluid or not) loads its 27 pull slots: they
-    // must lie inside the buffer and its margins
+    // must not precede the buffer (the step kernel's 32-bit offsets are
+    // unsigned) nor pass the end of its margin
     const int64_t margin = buffer_margin(nx);
     for (const int2 &c : ix.chunks) {
         const int32_t *nb = &ix.row_nb[(size_t)c.x * ROW_RECORD_INTS];
@@ -243,7 +248,7 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
         for (int l = 0; l < CHUNK; ++l)
             for (int i = 0; i < 27; ++i) {
                 const int64_t s = (int64_t)nb[i / 3] + x0 + l - (i % 3 - 1);
-                if (s < -margin || s >= ns + margin) return "chunk lane pull outside the buffer margins";
+                if (s < 0 || s >= ns + margin) return "chunk lane pull outside the buffer";
             }
         if ((int64_t)nb[4] + x0 < 0 || (int64_t)nb[4] + x0 + CHUNK > ns) return "chunk slots outside the buffer";
     }

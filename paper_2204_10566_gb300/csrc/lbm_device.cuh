@@ -1194,7 +1194,7 @@ void launch_fluid(const StepArgs &a, cudaStream_t s) {
 
 template <int P>
 cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s) {
-    const bool wide = a.stride > MAX_SLOTS_32;
+    const bool wide = a.wide_offsets || a.stride > MAX_SLOTS_32;
     const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
     if (a.nchunks > 0) {
         if (ghost1)

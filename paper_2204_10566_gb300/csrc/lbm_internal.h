@@ -104,7 +104,7 @@ struct alignas(16) StepArgs {
     const uint8_t *wall_q;     // records of 32 bytes: q = k / 256 of wall link i in byte i
     const int4 *wnodes;        // cells with interpolated walls (x, row, slot, record), out of the chunk lanes
     int32_t nwnodes;
-    int32_t reserved2_;
+    int32_t wide_offsets;      // 1: 64-bit element offsets even when 32 bits would do (LBM_WIDE_OFFSETS=1)
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).
