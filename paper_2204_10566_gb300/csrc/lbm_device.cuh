@@ -36,6 +36,14 @@
 #endif
 // The same for the kernel of the cells with interpolated walls, which keeps
 // the wall record and the own-slot values of a cell in registers as well.
+// In FP32 and FP16S the inlet/outlet nodes ride in trailing blocks of the
+// fluid kernel (one launch per step) instead of a launch of their own: +2 %
+// on the Re 3500 nozzle in FP32, although the node path spills at the fluid
+// path's register cap.  FP64 keeps the separate launch (its uncapped fluid
+// path would lose occupancy).
+#ifndef LBM_FUSE_BOUNDARY
+#define LBM_FUSE_BOUNDARY 1
+#endif
 #ifndef LBM_STEP_MIN_BLOCKS_WALLQ
 #define LBM_STEP_MIN_BLOCKS_WALLQ 4
 #endif
@@ -956,18 +964,22 @@ __device__ __forceinline__ void prefetch_block_sources(const StepArgs &a, int tb
 // gathers of later blocks find their rows in L2 instead of waiting on HBM.
 template <int P, bool GHOST1, bool WIDE>
 __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
-    const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
-    const int chunk = gt / CHUNK;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE>(a, chunk, gt % CHUNK, hv);
-    if (a.prefetch_ahead > 0) {
-        const int i = (int)threadIdx.x - (STEP_THREADS - 32);
-        if (i >= 0 && i < 27) prefetch_block_sources<P>(a, (int)blockIdx.x + a.prefetch_ahead, i);
+    if (LBM_FUSE_BOUNDARY && P != 0 && (int)blockIdx.x >= a.fluid_blocks) {  // inlet/outlet nodes, trailing blocks
+        const int k = ((int)blockIdx.x - a.fluid_blocks) * STEP_THREADS + (int)threadIdx.x;
+        if (k < a.nbnodes) boundary_node<P, GHOST1, WIDE>(a, k, hv);
+    } else {
+        const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
+        const int chunk = gt / CHUNK;
+        if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE>(a, chunk, gt % CHUNK, hv);
+        if (a.prefetch_ahead > 0) {
+            const int i = (int)threadIdx.x - (STEP_THREADS - 32);
+            if (i >= 0 && i < 27) prefetch_block_sources<P>(a, (int)blockIdx.x + a.prefetch_ahead, i);
+        }
     }
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
 
-// One time step of every inlet/outlet node of one lattice.
 // One time step of the cells with interpolated walls (see wall_cell); its
 // partial sums follow those of the fluid and inlet/outlet kernels.
 template <int P, bool GHOST1, bool WIDE>
@@ -981,6 +993,8 @@ __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS
     }
 }
 
+// One time step of every inlet/outlet node of one lattice (when they do not
+// ride in the trailing blocks of k_step).
 template <int P, bool GHOST1, bool WIDE>
 __global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
     const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
@@ -1187,7 +1201,8 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
 
 template <int P, bool G, bool WD>
 void launch_fluid(const StepArgs &a, cudaStream_t s) {
-    k_step<P, G, WD><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
+    const int bb = LBM_FUSE_BOUNDARY && P != 0 ? (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS) : 0;
+    k_step<P, G, WD><<<step_blocks(a.nchunks) + bb, STEP_THREADS, 0, s>>>(a);
     if (a.nwnodes > 0)  // cells with interpolated walls
         k_wall<P, G, WD><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
 }
@@ -1202,7 +1217,7 @@ cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s) {
         else
             wide ? launch_fluid<P, false, true>(a, s) : launch_fluid<P, false, false>(a, s);
     }
-    if (bb > 0) {
+    if (bb > 0 && !(LBM_FUSE_BOUNDARY && P != 0 && a.nchunks > 0)) {
         if (ghost1)
             wide ? k_boundary<P, true, true><<<bb, STEP_THREADS, 0, s>>>(a) : k_boundary<P, true, false><<<bb, STEP_THREADS, 0, s>>>(a);
         else
