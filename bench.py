@@ -99,12 +99,12 @@ def recorded_traffic(workload, precision):
 
 def launches_per_step(flags, periodic, precision="fp32"):
     """Kernels one lattice step launches: the fluid kernel, whose trailing
-    blocks update the inlet/outlet nodes in FP32 and FP16S; in FP64 the
+    blocks update the inlet/outlet nodes in FP32; in FP16S and FP64 the
     inlet/outlet kernel is a launch of its own when the geometry has such
     nodes."""
     from paper_2204_10566_gb300 import lbm
 
-    if precision != "fp64":
+    if precision == "fp32":
         return 1
     return 1 + (1 if lbm.check_layout(flags, periodic)["boundary_nodes"] > 0 else 0)
 

@@ -36,11 +36,11 @@
 #endif
 // The same for the kernel of the cells with interpolated walls, which keeps
 // the wall record and the own-slot values of a cell in registers as well.
-// In FP32 and FP16S the inlet/outlet nodes ride in trailing blocks of the
-// fluid kernel (one launch per step) instead of a launch of their own: +2 %
-// on the Re 3500 nozzle in FP32, although the node path spills at the fluid
-// path's register cap.  FP64 keeps the separate launch (its uncapped fluid
-// path would lose occupancy).
+// In FP32 the inlet/outlet nodes ride in trailing blocks of the fluid kernel
+// (one launch per step) instead of a launch of their own: +2 % on the Re 3500
+// nozzle, although the node path spills at the fluid path's register cap.
+// In FP16S the fused kernel spilled in the fluid path too, and FP64's
+// uncapped fluid path would lose occupancy, so both keep the separate launch.
 #ifndef LBM_FUSE_BOUNDARY
 #define LBM_FUSE_BOUNDARY 1
 #endif
@@ -965,7 +965,7 @@ __device__ __forceinline__ void prefetch_block_sources(const StepArgs &a, int tb
 template <int P, bool GHOST1, bool WIDE>
 __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (LBM_FUSE_BOUNDARY && P != 0 && (int)blockIdx.x >= a.fluid_blocks) {  // inlet/outlet nodes, trailing blocks
+    if (LBM_FUSE_BOUNDARY && P == 1 && (int)blockIdx.x >= a.fluid_blocks) {  // inlet/outlet nodes, trailing blocks
         const int k = ((int)blockIdx.x - a.fluid_blocks) * STEP_THREADS + (int)threadIdx.x;
         if (k < a.nbnodes) boundary_node<P, GHOST1, WIDE>(a, k, hv);
     } else {
@@ -1201,7 +1201,7 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
 
 template <int P, bool G, bool WD>
 void launch_fluid(const StepArgs &a, cudaStream_t s) {
-    const int bb = LBM_FUSE_BOUNDARY && P != 0 ? (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS) : 0;
+    const int bb = LBM_FUSE_BOUNDARY && P == 1 ? (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS) : 0;
     k_step<P, G, WD><<<step_blocks(a.nchunks) + bb, STEP_THREADS, 0, s>>>(a);
     if (a.nwnodes > 0)  // cells with interpolated walls
         k_wall<P, G, WD><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
@@ -1217,7 +1217,7 @@ cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s) {
         else
             wide ? launch_fluid<P, false, true>(a, s) : launch_fluid<P, false, false>(a, s);
     }
-    if (bb > 0 && !(LBM_FUSE_BOUNDARY && P != 0 && a.nchunks > 0)) {
+    if (bb > 0 && !(LBM_FUSE_BOUNDARY && P == 1 && a.nchunks > 0)) {
         if (ghost1)
             wide ? k_boundary<P, true, true><<<bb, STEP_THREADS, 0, s>>>(a) : k_boundary<P, true, false><<<bb, STEP_THREADS, 0, s>>>(a);
         else
