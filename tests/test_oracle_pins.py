@@ -688,3 +688,36 @@ def test_nozzle_voxel_counts():
     assert I.active_count(I.workload_flags("nozzle_re3500_96x96x800")) == 4286996
     f = I.workload_flags("nozzle_re500_24x24x160")
     assert (f[0] == 2).sum() == (f[1] != 0).sum() and (f[-1] == 3).sum() == (f[-2] != 0).sum()
+
+
+def test_wall_distances_of_a_round_pipe():
+    """inputs.nozzle_wall_q on a straight pipe of radius R: every wall link's
+    q is the root of |p_xy - s c_xy - centre| = R along the link, found in
+    closed form (quadratic), to within the 1/256 quantisation; links that
+    stay inside keep 128."""
+    D, L = 16, 6
+    cells, q = I.nozzle_wall_q(D, D, L, L_in=L, L_cone=1, L_throat=0)
+    flags = I.pipe_flags(D, L)
+    nz, ny, nx = flags.shape
+    c = np.array([[i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1] for i in range(27)], dtype=float)
+    R = D / 2.0
+    checked = 0
+    for b, row in zip(cells, q):
+        x, y, z = b % nx, (b // nx) % ny, b // (nx * ny)
+        assert flags[z, y, x] == 1
+        px, py = x + 0.5 - R, y + 0.5 - R
+        for i in range(27):
+            sx, sy, sz = x - int(c[i, 0]), y - int(c[i, 1]), z - int(c[i, 2])
+            inside_box = 0 <= sx < nx and 0 <= sy < ny and 0 <= sz < nz
+            solid = not inside_box or flags[sz, sy, sx] == 0
+            if not solid:
+                assert row[i] == 128
+                continue
+            # |(px - s cx, py - s cy)| = R, smallest root in (0, 1]
+            a = c[i, 0] ** 2 + c[i, 1] ** 2
+            bq = -2.0 * (px * c[i, 0] + py * c[i, 1])
+            cq = px * px + py * py - R * R
+            s = (-bq + math.sqrt(bq * bq - 4 * a * cq)) / (2 * a)
+            assert abs(row[i] / 256.0 - s) <= 0.5 / 256 + 1e-9, (b, i, row[i], s)
+            checked += 1
+    assert checked > 1000
