@@ -310,8 +310,9 @@ def serving_measurement(capacity_mlups, n_requests):
     throat diameter d, D = 3 d, L = 25 d, Re uniform in 500-6500, FP32 or
     FP16S with p = 1/2, Poisson arrivals at 1.2 x the measured single-stream
     FP32 capacity), against the same stream run back to back as plain FP32
-    lattices.  Sizes and step counts are scaled down from the full request
-    mix (d 8-48, 2000-20000 steps) so that the measurement takes seconds."""
+    lattices, and again at 0.5 x the capacity (latency of an unsaturated
+    server).  Sizes and step counts are scaled down from the full request mix
+    (d 8-48, 2000-20000 steps) so that the measurement takes seconds."""
     import torch
 
     from paper_2204_10566_gb300 import inputs as I
@@ -327,7 +328,14 @@ def serving_measurement(capacity_mlups, n_requests):
     free, _ = torch.cuda.mem_get_info()
     srv = serving.run_stream([dict(s) for s in specs], budget_bytes=int(0.5 * free), max_slots=32, steps_per_tick=32)
     b2b = serving.run_back_to_back([dict(s) for s in specs], "fp32")
+    # the same stream at 0.5x the capacity: latency when the server is not saturated
+    low = I.serving_requests(n=n_requests, seed=2204, rate=rate * 0.5 / 1.2, d_range=SERVING_D,
+                             steps_range=SERVING_STEPS)
+    srv_low = serving.run_stream([dict(s) for s in low], budget_bytes=int(0.5 * free), max_slots=32,
+                                 steps_per_tick=32)
     return {
+        "low_load": {"offered_load": 0.5, "p50_s": srv_low["latency_p50_s"], "p99_s": srv_low["latency_p99_s"],
+                     "aggregate_mlups": srv_low["mlups"]},
         "requests": n_requests, "arrival_rate_per_s": rate, "offered_load": 1.2,
         "stream": "seed 2204; d uniform in %d-%d (D = 3d, L = 25d), Re 500-6500, %d-%d steps, FP32/FP16S, "
                   "nozzle/pipe; scaled from d 8-48 and 2000-20000 steps" % (SERVING_D + SERVING_STEPS),
