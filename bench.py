@@ -300,6 +300,20 @@ class OracleSample:
         L.step(steps)
         return time.perf_counter() - t, int((f != 0).sum()) * steps
 
+    def single_thread(self):
+        """One oracle step on the first 16 z-planes of the slab with one
+        thread: returns (MLUPS, cells)."""
+        import numpy as np
+
+        plane = np.array(self.flags[:16])
+        L = self.oracle.Lattice(plane, self.omega, periodic=self.periodic, nthreads=1)
+        L.init_equilibrium(1.0, [0.0, 0.0, 0.01])
+        t = time.perf_counter()
+        L.step(1)
+        dt = time.perf_counter() - t
+        cells = int((plane != 0).sum())
+        return cells / dt / 1e6, cells
+
     def step(self):
         """One timed sample; returns (MLUPS, seconds)."""
         dt, updates = self._run(self.flags, self.steps)
@@ -447,8 +461,10 @@ def ours_arm(args):
     if world == 1 and not args.no_cpu_baseline:
         sample = OracleSample(flags, params, periodic, args.cpu_seconds)
         mlups, dt = sample.step()
+        st, st_cells = sample.single_thread()
         cpu = {"value": mlups, "unit": UNIT, "cores": sample.threads, "kind": "oracle", "sample": sample.desc,
-               "seconds": dt}
+               "seconds": dt, "single_thread": {"value": st, "unit": UNIT, "cores": 1,
+                                                "sample": "1 oracle step on 16 z-planes of the slab, %d active cells" % st_cells}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -459,6 +475,7 @@ def ours_arm(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "frac_of_nominal_7900": achieved / 7900.0,
                      "kernel": "k_step<%s>" % head,
                      "bytes_per_cell": algorithmic_bytes_per_cell(head)},
         "by_precision": by_prec,
