@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="oracle time of the whole --impl reference run (warm-up and timed steps)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
     return ap.parse_args()
@@ -378,7 +380,7 @@ def reference_arm(args):
     w, flags, params, periodic = workload_setup(args.workload)
     total = args.steps + args.warmup
     # each step a bounded sample, so that the whole run fits in ~150 s
-    sample = OracleSample(flags, params, periodic, max(0.002, 150.0 / max(total, 1)))
+    sample = OracleSample(flags, params, periodic, max(0.002, args.ref_seconds / max(total, 1)))
     vals = []
     t_all = 0.0
     for k in range(total):
