@@ -41,6 +41,13 @@
 // nozzle, although the node path spills at the fluid path's register cap.
 // In FP16S the fused kernel spilled in the fluid path too, and FP64's
 // uncapped fluid path would lose occupancy, so both keep the separate launch.
+// FP16S: gather and own-slot stores addressed from one pointer per line
+// (the three values of a line sit at +1, +stride, +2 stride - 1 from it):
+// +4 % / +7 % on the Re 3500 / Re 6500 nozzles, while FP32 lost 4 %, so FP32
+// keeps per-population offsets.
+#ifndef LBM_LINE_POINTERS
+#define LBM_LINE_POINTERS 1
+#endif
 #ifndef LBM_FUSE_BOUNDARY
 #define LBM_FUSE_BOUNDARY 1
 #endif
@@ -558,6 +565,20 @@ __device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], in
     using R = typename S::R;
     const T *fin = static_cast<const T *>(a.fin);
     const R inv_s = R(a.inv_scale);
+#if LBM_LINE_POINTERS
+    if constexpr (!WIDE && P == 2) {
+        // one pointer per line j; the three pulls sit at +1, +stride, +2 stride - 1
+        const uint32_t st = (uint32_t)a.stride;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const T *pj = fin + ((uint32_t)(3 * j) * st + (uint32_t)(nb[j] + x));
+            const T *q[3] = {pj + 1, pj + st, pj + 2 * st - 1};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d[3 * j + c] = RAW ? S::load_raw(q[c]) : S::load(q[c], inv_s);
+        }
+        return;
+    }
+#endif
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         const T *p = fin + elem<WIDE>(i, a.stride, nb[i / 3] + x - cx_of(i));
@@ -769,9 +790,27 @@ struct LineStore {
         if (own & OWN_FLUID) record_stress(a, slot, omega, a2);
     }
     __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const {
-        if (own & (1u << (3 * j))) put(3 * j, slot, vm);
-        if (own & (2u << (3 * j))) put(3 * j + 1, slot, v0);
-        if (own & (4u << (3 * j))) put(3 * j + 2, slot, vp);
+#if LBM_LINE_POINTERS
+        if constexpr (!WIDE && P == 2) {  // the three own-slot stores of line j from one pointer
+            const uint32_t st = (uint32_t)a.stride;
+            T *pj = static_cast<T *>(a.fout) + ((uint32_t)(3 * j) * st + (uint32_t)slot);
+            const R v[3] = {vm, v0, vp};
+            T *q[3] = {pj, pj + st, pj + 2 * st};
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (own & (1u << (3 * j + c))) {
+                    if constexpr (RAW)
+                        S::store_raw(q[c], v[c]);
+                    else
+                        S::store(q[c], v[c], R(a.scale));
+                }
+        } else
+#endif
+        {
+            if (own & (1u << (3 * j))) put(3 * j, slot, vm);
+            if (own & (2u << (3 * j))) put(3 * j + 1, slot, v0);
+            if (own & (4u << (3 * j))) put(3 * j + 2, slot, vp);
+        }
         const int jl = 8 - j;  // links 26 - i of this line's values sit in line 8 - j
         if (links & (7u << (3 * jl))) {
             const R v[3] = {vm, v0, vp};
