@@ -409,7 +409,9 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
             ++k;
         }
     }
-    // admit ready requests, first fit in submission order
+    // admit requests in submission order (the worker threads may finish the
+    // indexes out of order); a request that does not fit the memory left is
+    // passed over for later ones that do (first fit)
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         Request *r = s->reqs[*it].get();
         bool ready;
@@ -426,10 +428,7 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
             }
             continue;
         }
-        if (!ready) {
-            ++it;
-            continue;
-        }
+        if (!ready) break;  // admission keeps submission order: wait for this index
         if (!r->index_error.empty() || r->footprint > s->desc.budget_bytes) {
             r->state = LBM_REQ_FAILED;
             if (r->index_error.empty()) r->index_error = "footprint exceeds the memory budget";
