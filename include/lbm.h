@@ -191,6 +191,14 @@ lbm_status lbm_set_wall_q(lbm_ctx *ctx, const int64_t *cells, const uint8_t *q, 
  * |u_in| and u_char below the lattice sound speed 1/sqrt(3). */
 lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p);
 
+/* The checks of lbm_set_params without a context (host only, no device
+ * needed).  On LBM_OK, *nu receives the lattice viscosity (p->nu, or
+ * u_char L_char / Re, Sec. 2.2 Reynolds number) and *omega the relaxation
+ * rate 1/(3 nu + 1/2) (Sec. 2.1 relaxation time tau = nu / theta0 + 1/2);
+ * on LBM_ERR_ARG both receive 0.  *why receives a static string naming the
+ * failed check ("" on success).  Any of nu, omega, why may be NULL. */
+lbm_status lbm_params_check(const lbm_params *p, double *nu, double *omega, const char **why);
+
 /* The relaxation rate omega in use. */
 lbm_status lbm_get_omega(lbm_ctx *ctx, double *omega);
 

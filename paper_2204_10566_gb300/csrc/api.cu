@@ -284,6 +284,12 @@ bool ctx_ghost1(const lbm_ctx *c) { return c->ghost1; }
 int ctx_precision(const lbm_ctx *c) { return c->desc.precision; }
 int64_t ctx_slots(const lbm_ctx *c) { return c->idx.nslots; }
 
+float resolve_fp16_scale(float s) {
+    if (s == 0.0f) return 4096.0f;
+    int ex;
+    return (s > 0.0f && std::frexp(s, &ex) == 0.5f) ? s : 0.0f;
+}
+
 }  // namespace lbm
 
 extern "C" {
@@ -318,9 +324,8 @@ lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out) {
     if (desc->precision < LBM_FP64 || desc->precision > LBM_FP16S) return LBM_ERR_ARG;
     if (desc->periodic & ~7) return LBM_ERR_ARG;
     if ((desc->allocator.alloc == nullptr) != (desc->allocator.free == nullptr)) return LBM_ERR_ARG;
-    float s = desc->fp16_scale == 0.0f ? 4096.0f : desc->fp16_scale;
-    int ex;
-    if (!(s > 0.0f) || std::frexp(s, &ex) != 0.5f) return LBM_ERR_ARG;  // power of two
+    const float s = resolve_fp16_scale(desc->fp16_scale);
+    if (s == 0.0f) return LBM_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
         cudaGetLastError();
@@ -532,27 +537,49 @@ lbm_status lbm_fluid_count(lbm_ctx *c, int64_t *n) {
     return LBM_OK;
 }
 
+lbm_status lbm_params_check(const lbm_params *p, double *nu_out, double *omega_out, const char **why) {
+    const char *msg = "";
+    double nu = 0.0, omega = 0.0;
+    lbm_status st = LBM_ERR_ARG;
+    if (!p) {
+        msg = "params is NULL";
+    } else {
+        nu = p->nu;
+        if (!(nu > 0.0) && (!(p->Re > 0.0) || !(p->L_char > 0.0) || !(std::fabs(p->u_char) > 0.0))) {
+            msg = "give nu > 0, or Re, u_char and L_char > 0";
+        } else {
+            if (!(nu > 0.0)) nu = std::fabs(p->u_char) * p->L_char / p->Re;  // Re = u L / nu (Sec. 2.2)
+            omega = 1.0 / (3.0 * nu + 0.5);  // tau = nu / theta0 + 1/2 (Sec. 2.1)
+            const double g[4] = {p->omega3, p->omega4, p->omega5, p->omega6};
+            const double cs = 1.0 / std::sqrt(3.0);
+            if (!(omega > 0.0 && omega < 2.0))
+                msg = "omega outside (0, 2)";
+            else if (!std::all_of(g, g + 4, [](double r) { return r > 0.0 && r < 2.0; }))
+                msg = "ghost rates must lie in (0, 2)";
+            else if (!(std::fabs(p->u_in) < cs) || !(std::fabs(p->u_char) < cs))
+                msg = "velocities must stay below the lattice sound speed";
+            else if (p->inlet_profile != LBM_PROFILE_PLUG && p->inlet_profile != LBM_PROFILE_PARABOLIC)
+                msg = "unknown inlet profile";
+            else if (!(p->noise_amp >= 0.0) || !(p->rho_out > 0.0))
+                msg = "bad noise or rho_out";
+            else if (p->inlet_ramp < 0)
+                msg = "negative inlet ramp";
+            else
+                st = LBM_OK;
+        }
+    }
+    if (nu_out) *nu_out = st == LBM_OK ? nu : 0.0;
+    if (omega_out) *omega_out = st == LBM_OK ? omega : 0.0;
+    if (why) *why = msg;
+    return st;
+}
+
 lbm_status lbm_set_params(lbm_ctx *c, const lbm_params *p) {
     if (!c) return LBM_ERR_ARG;
-    if (!p) return fail(c, LBM_ERR_ARG, "params is NULL");
-    double nu = p->nu;
-    if (!(nu > 0.0)) {
-        if (!(p->Re > 0.0) || !(p->L_char > 0.0) || !(std::fabs(p->u_char) > 0.0))
-            return fail(c, LBM_ERR_ARG, "give nu > 0, or Re, u_char and L_char > 0");
-        nu = std::fabs(p->u_char) * p->L_char / p->Re;  // Re = u L / nu (Sec. 2.2)
-    }
-    const double omega = 1.0 / (3.0 * nu + 0.5);      // tau = nu / theta0 + 1/2 (Sec. 2.1)
-    if (!(omega > 0.0 && omega < 2.0)) return fail(c, LBM_ERR_ARG, "omega outside (0, 2)");
+    double nu, omega;
+    const char *why;
+    if (lbm_params_check(p, &nu, &omega, &why) != LBM_OK) return fail(c, LBM_ERR_ARG, why);
     const double g[4] = {p->omega3, p->omega4, p->omega5, p->omega6};
-    for (double r : g)
-        if (!(r > 0.0 && r < 2.0)) return fail(c, LBM_ERR_ARG, "ghost rates must lie in (0, 2)");
-    const double cs = 1.0 / std::sqrt(3.0);
-    if (!(std::fabs(p->u_in) < cs) || !(std::fabs(p->u_char) < cs))
-        return fail(c, LBM_ERR_ARG, "velocities must stay below the lattice sound speed");
-    if (p->inlet_profile != LBM_PROFILE_PLUG && p->inlet_profile != LBM_PROFILE_PARABOLIC)
-        return fail(c, LBM_ERR_ARG, "unknown inlet profile");
-    if (!(p->noise_amp >= 0.0) || !(p->rho_out > 0.0)) return fail(c, LBM_ERR_ARG, "bad noise or rho_out");
-    if (p->inlet_ramp < 0) return fail(c, LBM_ERR_ARG, "negative inlet ramp");
     c->params = *p;
     c->params.nu = nu;
     if (!(c->params.d_in > 0.0)) c->params.d_in = c->desc.nx;

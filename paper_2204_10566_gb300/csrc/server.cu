@@ -354,24 +354,11 @@ lbm_status lbm_server_submit(lbm_server *s, const lbm_request *q, int64_t *id) {
     const lbm_params &p = q->params;
     if (p.omega3 != 1.0 || p.omega4 != 1.0 || p.omega5 != 1.0 || p.omega6 != 1.0)
         return sfail(s, LBM_ERR_ARG, "the server runs the default ghost rates only");
-    {  // validate the parameters the way lbm_set_params does (host only)
-        lbm_desc d{};
-        d.nx = q->nx;
-        d.ny = q->ny;
-        d.nz = q->nz;
-        d.precision = q->precision;
-        d.fp16_scale = q->fp16_scale;
-        d.device = s->desc.device;
-        lbm_ctx *c = nullptr;
-        lbm_status st = lbm_create(&d, &c);
-        if (st != LBM_OK) return sfail(s, st, "bad lattice description");
-        st = lbm_set_params(c, &p);
-        if (st != LBM_OK) {
-            s->err = lbm_last_error(c);
-            lbm_destroy(c);
-            return st;
-        }
-        lbm_destroy(c);
+    if (resolve_fp16_scale(q->fp16_scale) == 0.0f)
+        return sfail(s, LBM_ERR_ARG, "the FP16 scale must be 0 (default) or a power of two");
+    {  // the checks of lbm_set_params, on the host
+        const char *why;
+        if (lbm_params_check(&p, nullptr, nullptr, &why) != LBM_OK) return sfail(s, LBM_ERR_ARG, why);
     }
     const int64_t ncell = (int64_t)q->nx * q->ny * q->nz;
     int64_t active = 0;

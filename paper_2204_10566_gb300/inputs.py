@@ -161,6 +161,13 @@ WORKLOADS = {
 }
 
 
+# Throat diameters (cells) of the resolution ladder R1-R3 (Sec. 3).  The
+# grid spacings of Table 2, 2.3, 1.725 and 1.15 (x 1e-4 m), on the 4 mm
+# throat give 17.4, 23.2 and 34.8 cells; these are rounded up to multiples
+# of 6, which keeps the table's spacing ratios 1 : 4/3 : 2 exactly.
+LADDER_THROAT_CELLS = (18, 24, 36)
+
+
 def workload_flags(name):
     w = WORKLOADS[name]
     if w["kind"] == "nozzle":

@@ -101,6 +101,7 @@ _SIGS = {
     "lbm_fluid_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "lbm_set_wall_q": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "lbm_set_params": (C.c_int, [C.c_void_p, C.POINTER(lbm_params)]),
+    "lbm_params_check": (C.c_int, [C.POINTER(lbm_params), _dp, _dp, C.POINTER(C.c_char_p)]),
     "lbm_get_omega": (C.c_int, [C.c_void_p, _dp]),
     "lbm_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, _dp]),
     "lbm_init_fields": (C.c_int, [C.c_void_p, _dp, _dp, C.c_int32]),
@@ -175,6 +176,36 @@ def make_params(nu=0.0, Re=0.0, u_char=0.0, L_char=0.0, ghost=(1.0, 1.0, 1.0, 1.
     p.inlet_profile = PROFILES[profile] if isinstance(profile, str) else int(profile)
     p.inlet_ramp = int(inlet_ramp)
     return p
+
+
+def params_check(p):
+    """lbm_params_check: (nu, omega) of a parameter set, on the host; raises
+    LbmError naming the failed check."""
+    nu, omega, why = C.c_double(), C.c_double(), C.c_char_p()
+    st = capi().lbm_params_check(C.byref(p), C.byref(nu), C.byref(omega), C.byref(why))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_params_check: " + why.value.decode())
+    return nu.value, omega.value
+
+
+def lattice_units(Re, delta_r, delta_t, rho, mu, d_thr):
+    """Lattice parameters of a run given in physical units (SI) (Sec. 2.2).
+    The Reynolds number on the throat fixes the throat mean velocity
+    u_thr = mu Re / (rho d_thr); in cells and steps the characteristic length
+    is L_char = d_thr / delta_r, the velocity u_char = u_thr delta_t / delta_r
+    (half the CFL number of Sec. 2.2) and the viscosity
+    nu = mu delta_t / (rho delta_r^2).  Returns a dict with Re, L_char,
+    u_char, nu and CFL; Re, u_char and L_char feed make_params."""
+    u_thr = mu * Re / (rho * d_thr)
+    u_char = u_thr * delta_t / delta_r
+    return dict(Re=Re, L_char=d_thr / delta_r, u_char=u_char, nu=mu * delta_t / (rho * delta_r ** 2),
+                CFL=2.0 * u_char)
+
+
+def cfl_time_step(Re, delta_r, CFL, rho, mu, d_thr):
+    """Time step (s) that puts the throat mean velocity at the given CFL
+    number, CFL = 2 u_thr delta_t / delta_r (Sec. 2.2 time-step rule)."""
+    return rho * d_thr * delta_r * CFL / (2.0 * mu * Re)
 
 
 def make_nozzle(D, d, L_total, L_in=None, L_cone=-1, L_throat=None, half_angle_deg=10.0):

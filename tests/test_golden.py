@@ -1,0 +1,141 @@
+"""Pins against numbers the paper prints (fixtures under tests/golden/).
+
+table2_resolutions.txt, Table 2 (Sec. 2.2): the printed time steps follow
+the CFL rule of Sec. 2.2 with one CFL number per Reynolds number, and the
+lattice parameters the library derives from (Re, u_char, L_char) reproduce
+the relaxation time of Sec. 2.1 computed from the physical viscosity.
+
+d3q27_weights_1d.txt, Appendix A: the oracle's D3Q27 weights are the
+products of the printed 1-D weights, and its stencil temperature the printed
+theta0.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2204_10566_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+# Fluid and throat of Sec. 2.2 (SI): density, dynamic viscosity, throat
+# diameter (a 0.012 m domain and an inlet-to-throat diameter ratio of 3).
+RHO, MU, D_THR = 1056.0, 3.5e-3, 0.004
+
+
+def data_lines(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.lstrip().startswith("#")]
+
+
+def table2():
+    """Rows (level, Re, delta_r [m], delta_t [s]) of Table 2."""
+    return [(lv, float(re_), float(dr) * 1e-4, float(dt) * 1e-6) for lv, re_, dr, dt in data_lines("table2_resolutions.txt")]
+
+
+def cfl_of(Re, dr, dt):
+    """CFL number of a row: the time-step rule of Sec. 2.2 solved for CFL."""
+    return 2.0 * MU * Re * dt / (RHO * D_THR * dr)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2204_10566_gb300 import build
+
+    build.build()
+    from paper_2204_10566_gb300 import lbm as m
+
+    return m
+
+
+def test_table2_time_steps_follow_the_cfl_rule(lbm):
+    rows = table2()
+    assert len(rows) == 10
+    groups = {}
+    for lv, Re, dr, dt in rows:
+        if lv != "R4":
+            groups.setdefault(Re, []).append((dr, dt))
+    cfl = {Re: np.mean([cfl_of(Re, dr, dt) for dr, dt in g]) for Re, g in groups.items()}
+    # one CFL number per Reynolds number: every printed delta_t of R1-R3 is
+    # the rule's time step at that CFL to within the table's rounding (0.25 %)
+    for lv, Re, dr, dt in rows:
+        if lv == "R4":
+            continue
+        pred = lbm.cfl_time_step(Re, dr, cfl[Re], RHO, MU, D_THR)
+        assert abs(pred / dt - 1.0) < 2.5e-3, (lv, Re, pred, dt)
+    # the transitional and turbulent runs share their CFL number; the laminar
+    # run takes a smaller one
+    assert abs(cfl[3500.0] / cfl[6500.0] - 1.0) < 2.5e-3
+    assert cfl[500.0] < 0.75 * cfl[3500.0]
+    # R4 of the Re 6500 runs does not follow the rule at that CFL: the printed
+    # 1.7e-6 s is 5 % below the 1.79e-6 s it gives (a typo or another CFL)
+    lv, Re, dr, dt = rows[-1]
+    assert lv == "R4"
+    pred = lbm.cfl_time_step(Re, dr, cfl[Re], RHO, MU, D_THR)
+    assert 0.04 < pred / dt - 1.0 < 0.06
+
+
+def test_table2_lattice_parameters_give_the_relaxation_time(lbm):
+    for lv, Re, dr, dt in table2():
+        lu = lbm.lattice_units(Re, dr, dt, RHO, MU, D_THR)
+        assert abs(lu["CFL"] - cfl_of(Re, dr, dt)) < 1e-12
+        # the library's route: nu = u_char L_char / Re, omega = 1 / (3 nu + 1/2)
+        p = lbm.make_params(Re=lu["Re"], u_char=lu["u_char"], L_char=lu["L_char"])
+        nu, omega = lbm.params_check(p)
+        # the paper's route in physical units (Sec. 2.1): tau = mu / (rho theta0) + dt / 2
+        # with theta0 = dr^2 / (3 dt^2); omega = dt / tau
+        theta0 = dr ** 2 / (3.0 * dt ** 2)
+        tau = MU / (RHO * theta0) + dt / 2.0
+        assert abs(omega / (dt / tau) - 1.0) < 1e-12, (lv, Re)
+        assert abs(nu / lu["nu"] - 1.0) < 1e-12
+        # under-resolved regime of the paper: tau close to 1/2
+        assert 0.5 < 1.0 / omega < 0.52
+
+
+def test_ladder_levels_follow_table2():
+    rows = [r for r in table2() if r[1] == 3500.0]
+    d_cells = [D_THR / dr for _, _, dr, _ in rows]
+    lad = I.LADDER_THROAT_CELLS
+    for d_tab, d_lad in zip(d_cells, lad):
+        assert d_tab <= d_lad < 1.04 * d_tab
+    for k in (1, 2):
+        assert abs(d_cells[k] / d_cells[0] - lad[k] / lad[0]) < 1e-12
+
+
+def test_params_check_on_the_host(lbm):
+    nu, omega = lbm.params_check(lbm.make_params(nu=0.01))
+    assert nu == 0.01 and abs(omega - 1.0 / 0.53) < 1e-15
+    # nu given wins over (Re, u_char, L_char)
+    assert lbm.params_check(lbm.make_params(nu=0.02, Re=100.0, u_char=0.05, L_char=10.0))[0] == 0.02
+    bad = [
+        (dict(), "give nu"),
+        (dict(Re=100.0, u_char=0.05), "give nu"),
+        (dict(nu=-0.2), "give nu"),
+        (dict(nu=1e-9, ghost=(1.0, 2.0, 1.0, 1.0)), "ghost rates"),
+        (dict(nu=0.01, u_in=0.6), "sound speed"),
+        (dict(Re=10.0, u_char=0.6, L_char=10.0), "sound speed"),
+        (dict(nu=0.01, profile=7), "profile"),
+        (dict(nu=0.01, noise_amp=-0.1), "noise"),
+        (dict(nu=0.01, rho_out=0.0), "rho_out"),
+        (dict(nu=0.01, inlet_ramp=-1), "ramp"),
+    ]
+    for kw, word in bad:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.params_check(lbm.make_params(**kw))
+        assert e.value.status == lbm.LBM_ERR_ARG and word in str(e.value), (kw, str(e.value))
+
+
+def test_weights_are_products_of_the_printed_1d_weights(orc):
+    table = {k: Fraction(v) for k, v in data_lines("d3q27_weights_1d.txt")}
+    w1 = {int(k): v for k, v in table.items() if k != "theta0"}
+    assert sum(w1.values()) == 1
+    c = orc.velocities()
+    w = orc.weights()
+    for i in range(27):
+        exact = w1[int(c[i][0])] * w1[int(c[i][1])] * w1[int(c[i][2])]
+        assert abs(w[i] - float(exact)) <= 2.0 ** -53 * float(exact), i
+    # theta0 is the second moment of the 1-D weights (Appendix A)
+    theta0 = table["theta0"]
+    assert sum(v * k * k for k, v in w1.items()) == theta0
+    th = np.einsum("i,i->", w, c[:, 0].astype(float) ** 2)
+    assert abs(th - float(theta0)) < 1e-16

@@ -60,7 +60,7 @@ def ladder_level(lbm, d, smooth, flow_units=30.0, u=0.05, Re=3500.0):
 
 def test_resolution_ladder_converges(lbm):
     smooth = True
-    levels = [ladder_level(lbm, d, smooth) for d in (18, 24, 36)]
+    levels = [ladder_level(lbm, d, smooth) for d in I.LADDER_THROAT_CELLS]
     z_exp = min(lv[2] for lv in levels)
     zq = np.linspace(0.5, z_exp - 0.5, 200)
     prof = [np.interp(zq, z, u) for z, u, _ in levels]

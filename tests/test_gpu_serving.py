@@ -95,6 +95,12 @@ def test_submit_rejects_bad_requests(mods):
         with pytest.raises(lbm.LbmError) as e:
             srv.submit(small, 10, "fp32", nu=-1.0)
         assert e.value.status == lbm.LBM_ERR_ARG
+        with pytest.raises(lbm.LbmError) as e:
+            srv.submit(small, 10, "fp16s", nu=0.01, fp16_scale=3000.0)
+        assert e.value.status == lbm.LBM_ERR_ARG and "power of two" in str(e.value)
+        with pytest.raises(lbm.LbmError) as e:
+            srv.submit(small, 10, "fp32", nu=0.01, u_in=0.7)
+        assert e.value.status == lbm.LBM_ERR_ARG and "sound speed" in str(e.value)
     finally:
         srv.close()
 
