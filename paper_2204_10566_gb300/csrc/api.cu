@@ -284,6 +284,9 @@ bool ctx_ghost1(const lbm_ctx *c) { return c->ghost1; }
 int ctx_precision(const lbm_ctx *c) { return c->desc.precision; }
 int64_t ctx_slots(const lbm_ctx *c) { return c->idx.nslots; }
 
+// FP16S scale of a descriptor: 0 selects the default 4096, any other value
+// must be a positive power of two (so that scaling is exact).  Returns the
+// scale, or 0 when the value is invalid.
 float resolve_fp16_scale(float s) {
     if (s == 0.0f) return 4096.0f;
     int ex;

@@ -45,11 +45,6 @@ enum : uint32_t {
 
 enum : int { STEP_REDUCE = 1, STEP_STATS = 2, STEP_STATS_FULL = 4 };
 
-// FP16S scale of a descriptor: 0 selects the default 4096, any other value
-// must be a positive power of two (so that scaling is exact).  Returns the
-// scale, or 0 when the value is invalid.
-float resolve_fp16_scale(float s);
-
 // Statistics accumulators, [components][slots] doubles: 0 sum u_z, 1 sum u_z^2
 // (always), and with full statistics 2..4 sum u, 5..10 sum u_a u_b
 // (xx, yy, zz, xy, xz, yz), 11..16 sum sigma_ab (same order), 17 sum rho.

@@ -30,6 +30,10 @@
 
 namespace lbm {
 
+// FP16S scale of a descriptor (api.cu): 0 selects the default 4096, any
+// other value must be a positive power of two; returns 0 when invalid.
+float resolve_fp16_scale(float s);
+
 constexpr int MAX_SLOTS = LBM_SERVER_MAX_SLOTS;
 constexpr int NGROUPS = 2;  // 0: FP32, 1: FP16S
 
