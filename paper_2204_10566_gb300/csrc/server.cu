@@ -241,6 +241,13 @@ lbm_status capture_tick(lbm_server *s) {
     return LBM_OK;
 }
 
+// The copied flags and the host index are needed only until admission.
+void drop_inputs(Request *r) {
+    std::vector<uint8_t>().swap(r->flags);
+    r->req.flags = nullptr;
+    r->idx = HostIndex();
+}
+
 void release(lbm_server *s, Request *r) {
     if (r->ctx) {
         lbm_destroy(r->ctx);
@@ -269,10 +276,12 @@ lbm_status admit(lbm_server *s, Request *r) {
     if (st != LBM_OK) {
         r->index_error = c ? lbm_last_error(c) : "context creation failed";
         if (c) lbm_destroy(c);
+        drop_inputs(r);
         r->state = LBM_REQ_FAILED;
         return st;
     }
     r->ctx = c;
+    drop_inputs(r);
     r->group = r->req.precision == LBM_FP16S ? 1 : 0;
     r->state = LBM_REQ_RUNNING;
     s->in_use += r->footprint;
@@ -299,16 +308,32 @@ lbm_status lbm_server_create(const lbm_server_desc *desc, lbm_server **out) {
     std::unique_ptr<lbm_server> s(new lbm_server());
     s->desc = *desc;
     cudaSetDevice(desc->device);
+    // on a failure below, free what was made so far (no worker runs yet)
+    auto undo = [&](lbm_status st) {
+        for (int q = 0; q < NGROUPS; ++q) {
+            if (s->h_tab[q]) cudaFreeHost(s->h_tab[q]);
+            if (s->d_tab[q]) cudaFree(s->d_tab[q]);
+        }
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        cudaGetLastError();
+        return st;
+    };
     s->stream = static_cast<cudaStream_t>(desc->stream);
     if (!s->stream) {  // graphs cannot be captured on the legacy default stream
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return LBM_ERR_CUDA;
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return undo(LBM_ERR_CUDA);
         s->own_stream = true;
     }
     for (int q = 0; q < NGROUPS; ++q) {
-        if (cudaMallocHost(&s->h_tab[q], sizeof(GroupTable)) != cudaSuccess) return LBM_ERR_CUDA;
+        if (cudaMallocHost(&s->h_tab[q], sizeof(GroupTable)) != cudaSuccess) {
+            s->h_tab[q] = nullptr;
+            return undo(LBM_ERR_CUDA);
+        }
         memset(s->h_tab[q], 0, sizeof(GroupTable));
         // the tables are part of the server, not of any lattice: not from the allocator
-        if (cudaMalloc(&s->d_tab[q], sizeof(GroupTable)) != cudaSuccess) return LBM_ERR_OOM;
+        if (cudaMalloc(&s->d_tab[q], sizeof(GroupTable)) != cudaSuccess) {
+            s->d_tab[q] = nullptr;
+            return undo(LBM_ERR_OOM);
+        }
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, desc->device);
@@ -413,6 +438,7 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
         if (r->cancel) {
             if (ready) {  // the worker is done with it
                 r->state = LBM_REQ_CANCELLED;
+                drop_inputs(r);
                 it = s->queue.erase(it);
             } else {
                 ++it;
@@ -422,6 +448,7 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
         if (!ready) break;  // admission keeps submission order: wait for this index
         if (!r->index_error.empty() || r->footprint > s->desc.budget_bytes) {
             r->state = LBM_REQ_FAILED;
+            drop_inputs(r);
             if (r->index_error.empty()) r->index_error = "footprint exceeds the memory budget";
             it = s->queue.erase(it);
             continue;
