@@ -43,38 +43,43 @@ def lib():
     """Load (building first if needed) the oracle shared library."""
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        dp = C.POINTER(C.c_double)
-        L.orc_velocity.argtypes = [C.c_int, C.POINTER(C.c_int)]
-        L.orc_weight.argtypes = [C.c_int]
-        L.orc_weight.restype = C.c_double
-        L.orc_hermite.argtypes = [C.POINTER(C.c_int), C.c_int, dp]
-        L.orc_hermite.restype = C.c_double
-        L.orc_hermite_m.argtypes = [C.c_int, dp]
-        L.orc_hermite_m.restype = C.c_double
-        L.orc_transform.argtypes = [dp, dp]
-        L.orc_equilibrium.argtypes = [C.c_double, dp, dp]
-        L.orc_equilibrium_tuples.argtypes = [C.c_double, dp, dp]
-        L.orc_solve.argtypes = [dp, dp, C.c_int]
-        L.orc_solve.restype = C.c_int
-        L.orc_moments.argtypes = [dp, dp]
-        L.orc_collide.argtypes = [dp, C.c_double, dp, C.c_double, dp, dp]
-        L.orc_collide.restype = C.c_int
-        L.orc_splitmix64.argtypes = [C.c_uint64]
-        L.orc_splitmix64.restype = C.c_uint64
-        L.orc_noise.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int]
-        L.orc_noise.restype = C.c_double
-        L.orc_step.argtypes = [C.POINTER(_Lattice), dp, dp, dp, C.c_int64]
-        L.orc_step.restype = C.c_int
-        L.orc_field_moments.argtypes = [C.POINTER(_Lattice), dp, dp]
-        L.orc_viscous_stress.argtypes = [dp, C.c_double, dp]
-        L.orc_field_stress.argtypes = [C.POINTER(_Lattice), dp, dp]
-        L.orc_totals.argtypes = [C.POINTER(_Lattice), dp, dp]
-        L.orc_nee_neighbour.argtypes = [C.POINTER(_Lattice), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
-        L.orc_nee_neighbour.restype = C.c_int64
-        _lib = L
+        _lib = declare(C.CDLL(_build.build()))
     return _lib
+
+
+def declare(L):
+    """Declare the argument and result types of the oracle's C functions on a
+    loaded library (also used by the tests that load deliberately broken
+    copies of the oracle)."""
+    dp = C.POINTER(C.c_double)
+    L.orc_velocity.argtypes = [C.c_int, C.POINTER(C.c_int)]
+    L.orc_weight.argtypes = [C.c_int]
+    L.orc_weight.restype = C.c_double
+    L.orc_hermite.argtypes = [C.POINTER(C.c_int), C.c_int, dp]
+    L.orc_hermite.restype = C.c_double
+    L.orc_hermite_m.argtypes = [C.c_int, dp]
+    L.orc_hermite_m.restype = C.c_double
+    L.orc_transform.argtypes = [dp, dp]
+    L.orc_equilibrium.argtypes = [C.c_double, dp, dp]
+    L.orc_equilibrium_tuples.argtypes = [C.c_double, dp, dp]
+    L.orc_solve.argtypes = [dp, dp, C.c_int]
+    L.orc_solve.restype = C.c_int
+    L.orc_moments.argtypes = [dp, dp]
+    L.orc_collide.argtypes = [dp, C.c_double, dp, C.c_double, dp, dp]
+    L.orc_collide.restype = C.c_int
+    L.orc_splitmix64.argtypes = [C.c_uint64]
+    L.orc_splitmix64.restype = C.c_uint64
+    L.orc_noise.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int]
+    L.orc_noise.restype = C.c_double
+    L.orc_step.argtypes = [C.POINTER(_Lattice), dp, dp, dp, C.c_int64]
+    L.orc_step.restype = C.c_int
+    L.orc_field_moments.argtypes = [C.POINTER(_Lattice), dp, dp]
+    L.orc_viscous_stress.argtypes = [dp, C.c_double, dp]
+    L.orc_field_stress.argtypes = [C.POINTER(_Lattice), dp, dp]
+    L.orc_totals.argtypes = [C.POINTER(_Lattice), dp, dp]
+    L.orc_nee_neighbour.argtypes = [C.POINTER(_Lattice), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
+    L.orc_nee_neighbour.restype = C.c_int64
+    return L
 
 
 def _dp(a):

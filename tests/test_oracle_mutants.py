@@ -1,0 +1,171 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each case plants one mistake in a copy of oracle/lbm_oracle.c: a dropped
+term, a wrong sign, index or constant, a transposed operand, a missing
+factor.  The copy is compiled into a library of its own, the oracle's
+Python wrappers are pointed at it, and the pins named for the case run
+against it: at least one of them must fail.  The real oracle passes all of
+them (tests/test_oracle_pins.py).
+"""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "lbm_oracle.c")
+G0, G1 = (1.0, 1.0, 1.0, 1.0), (0.8, 1.2, 1.5, 0.5)
+
+# name: (mistake, text in the oracle, planted text, pins expected to catch it)
+MUTANTS = {
+    "one_d_weight": (
+        "1-D weight of c = +-1 mistyped (Appendix A)",
+        "? 2.0 / 3.0 : 1.0 / 6.0", "? 2.0 / 3.0 : 1.0 / 5.0",
+        [("test_weights_quadrature_moments",), ("test_central_equilibrium_moments_vanish", 0)]),
+    "hermite_cyc_sign": (
+        "wrong sign of the delta terms of the Hermite polynomials (Appendix A)",
+        "r -= ORC_THETA0 * orc_hermite(rest, n - 2, xi);", "r += ORC_THETA0 * orc_hermite(rest, n - 2, xi);",
+        [("test_hermite_matches_printed_forms",), ("test_central_equilibrium_moments_vanish", 0)]),
+    "equilibrium_second_order_only": (
+        "equilibrium truncated at second order instead of the full expansion (Appendix A)",
+        "g_eq_prefactor[m] = mult / (factorial(n) * pow(ORC_THETA0, n));",
+        "g_eq_prefactor[m] = n > 2 ? 0.0 : mult / (factorial(n) * pow(ORC_THETA0, n));",
+        [("test_central_equilibrium_moments_vanish", 0), ("test_equilibrium_closed_forms", 0)]),
+    "equilibrium_multiplicity": (
+        "index tuples of one multi-index counted once (Sec. 2.1 equilibrium sum)",
+        "double mult = factorial(n) / (factorial(deg[0]) * factorial(deg[1]) * factorial(deg[2]));",
+        "double mult = 1.0;",
+        [("test_equilibrium_closed_forms", 0), ("test_central_equilibrium_moments_vanish", 0)]),
+    "central_shift_sign": (
+        "moments taken about c + u instead of c - u (Sec. 2.1 central moments)",
+        "double xi[3] = {c[0] - u[0], c[1] - u[1], c[2] - u[2]};",
+        "double xi[3] = {c[0] + u[0], c[1] + u[1], c[2] + u[2]};",
+        [("test_central_equilibrium_moments_vanish", 0), ("test_collision_relaxes_each_central_moment", G0)]),
+    "off_diagonal_rate": (
+        "off-diagonal second-order moments relaxed at 1 instead of omega (Appendix A)",
+        "    if (n == 2) return omega;", "    if (n == 2) return (m == 2 || m == 6 || m == 18) ? omega : 1.0;",
+        [("test_collision_reduces_to_bgk", 0.6), ("test_collision_relaxes_each_central_moment", G0)]),
+    "ghost_rate_order": (
+        "ghost rates assigned to the wrong orders",
+        "    return ghost[n - 3];", "    return ghost[6 - n];",
+        [("test_collision_relaxes_each_central_moment", G1)]),
+    "momentum_for_velocity": (
+        "rho u used where u is meant",
+        "mom[1 + a] = j[a] / rho;", "mom[1 + a] = j[a];",
+        [("test_collision_conserves_mass_momentum", 0)]),
+    "solve_rhs_not_swapped": (
+        "pivoting swaps the rows of the matrix but not of the right-hand side",
+        "            double t = b[k]; b[k] = b[p]; b[p] = t;", "            (void)0;",
+        [("test_gaussian_elimination_matches_lapack",), ("test_collision_conserves_mass_momentum", 1)]),
+    "push_for_pull": (
+        "streaming gathers from x + c_i instead of x - c_i",
+        "int fl = flag_at(L, x - c[0], y - c[1], z - c[2], &src);",
+        "int fl = flag_at(L, x + c[0], y + c[1], z + c[2], &src);",
+        [("test_streaming_pull_and_bounce_back", 0), ("test_viscous_stress_shear_wave",)]),
+    "bounce_back_same_direction": (
+        "a wall link returns population i instead of its opposite (Sec. 2.2 bounce-back)",
+        "const int ib = ORC_Q - 1 - i;", "const int ib = i;",
+        [("test_closed_box_conserves_mass",), ("test_streaming_pull_and_bounce_back", 0)]),
+    "bouzidi_near_weights_swapped": (
+        "the two weights of Bouzidi's q < 1/2 interpolation exchanged",
+        "fi = 2.0 * q * fin[self * ORC_Q + ib] + (1.0 - 2.0 * q) * fin[nbr * ORC_Q + ib];",
+        "fi = (1.0 - 2.0 * q) * fin[self * ORC_Q + ib] + 2.0 * q * fin[nbr * ORC_Q + ib];",
+        [("test_interpolated_bounce_back_places_the_walls",)]),
+    "bouzidi_far_wrong_population": (
+        "Bouzidi's q >= 1/2 form mixes with f_ib instead of f_i",
+        "fi = fin[self * ORC_Q + ib] / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * fin[self * ORC_Q + i];",
+        "fi = fin[self * ORC_Q + ib] / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * fin[self * ORC_Q + ib];",
+        [("test_interpolated_bounce_back_places_the_walls",)]),
+    "nee_sign": (
+        "non-equilibrium part subtracted instead of added (Sec. 2.2 NEE)",
+        "fout[b * ORC_Q + i] = feq_b[i] + (fout[bf * ORC_Q + i] - feq_f[i]);",
+        "fout[b * ORC_Q + i] = feq_b[i] - (fout[bf * ORC_Q + i] - feq_f[i]);",
+        [("test_nee_boundary_nodes",)]),
+    "outlet_density": (
+        "outlet takes the partner's density instead of the imposed one",
+        "rho_b = L->rho_out;", "rho_b = rho_f;",
+        [("test_nee_boundary_nodes",)]),
+    "inlet_density": (
+        "inlet density fixed at 1 instead of extrapolated",
+        "            rho_b = rho_f;\n            orc_inlet_velocity", "            rho_b = 1.0;\n            orc_inlet_velocity",
+        [("test_nee_boundary_nodes",)]),
+    "parabola": (
+        "parabolic inlet profile with 2 r^2 instead of 4 r^2 (Sec. 2.2 inlet profile)",
+        "(1.0 - 4.0 * r2 / (L->d_in * L->d_in))", "(1.0 - 2.0 * r2 / (L->d_in * L->d_in))",
+        [("test_nee_boundary_nodes",)]),
+    "ramp_shape": (
+        "start-up ramp s^2 instead of s^2 (3 - 2 s)",
+        "double r = s * s * (3.0 - 2.0 * s);", "double r = s * s;",
+        [("test_inlet_start_up_ramp",)]),
+    "noise_bits": (
+        "noise keeps 23 bits instead of 24",
+        "(double)(h >> 40) * (1.0 / 8388608.0) - 1.0", "(double)(h >> 41) * (1.0 / 8388608.0) - 1.0",
+        [("test_noise_uniform",)]),
+    "splitmix_constant": (
+        "a SplitMix64 multiplier mistyped",
+        "z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;", "z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b8ULL;",
+        [("test_splitmix64_reference_outputs",)]),
+    "noise_ignores_seed": (
+        "the seed's hash dropped from the noise counter chain",
+        "h = orc_splitmix64((uint64_t)step + h);", "h = orc_splitmix64((uint64_t)step);",
+        [("test_noise_depends_on_every_counter",)]),
+    "stress_sign": (
+        "strain rate without the minus sign (Appendix A strain-rate relation)",
+        "const double S = -a / (2.0 * rho * ORC_THETA0 * tau);", "const double S = a / (2.0 * rho * ORC_THETA0 * tau);",
+        [("test_viscous_stress_shear_wave",)]),
+    "stress_theta_term": (
+        "theta0 delta_ab left out of the second-order Hermite moment",
+        "            if (pa[k] == pb[k]) h -= ORC_THETA0;", "            if (pa[k] == pb[k]) h -= 0.0;",
+        [("test_viscous_stress_of_equilibrium_is_zero",)]),
+    "node_stress_dropped": (
+        "inlet/outlet nodes report no stress instead of their partner's",
+        "for (int k = 0; k < 6; ++k) sigma[b * 6 + k] = sigma[bf * 6 + k];",
+        "for (int k = 0; k < 6; ++k) sigma[b * 6 + k] = 0.0;",
+        [("test_square_duct_poiseuille_profile",)]),
+    "totals_uncompensated": (
+        "compensation dropped from the FP64 totals",
+        "comp[k] = (t - s[k]) - y;", "comp[k] = 0.0;",
+        [("test_totals_compensated_on_an_ill_conditioned_sum",)]),
+}
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+def build_mutant(directory, name, old, new):
+    text = open(SRC).read()
+    assert text.count(old) == 1, "the oracle text of %s is no longer unique" % name
+    src = os.path.join(str(directory), name + ".c")
+    lib = os.path.join(str(directory), name + ".so")
+    with open(src, "w") as fh:
+        fh.write(text.replace(old, new))
+    flags = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    r = subprocess.run(["gcc"] + flags + ["-fopenmp", src, "-o", lib, "-lm"], capture_output=True)
+    if r.returncode != 0:  # OpenMP is optional, as for the oracle itself
+        subprocess.run(["gcc"] + flags + [src, "-o", lib, "-lm"], check=True, capture_output=True)
+    return lib
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(mutant_dir, name):
+    what, old, new, catchers = MUTANTS[name]
+    lib = build_mutant(mutant_dir, name, old, new)
+    saved = oracle.lib()
+    oracle._lib = oracle.declare(C.CDLL(lib))
+    caught = []
+    try:
+        with np.errstate(all="ignore"):
+            for pin, *args in catchers:
+                try:
+                    getattr(pins, pin)(oracle, *args)
+                except (AssertionError, RuntimeError, ValueError, ArithmeticError, np.linalg.LinAlgError):
+                    caught.append(pin)  # a failed check, or the broken oracle failing outright
+    finally:
+        oracle._lib = saved
+    assert caught, "no pin caught: " + what

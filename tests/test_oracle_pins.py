@@ -523,6 +523,13 @@ def test_square_duct_poiseuille_profile(orc):
     # velocity, not the streamed flux)
     flux = (m[1:-1, ..., 0] * m[1:-1, ..., 3]).sum(axis=(1, 2))
     assert np.ptp(flux) < 1e-6 * flux.mean()
+    # the outlet nodes carry the stress of the developed flow: the wall shear
+    # sigma_xz, sigma_yz on the outlet plane matches that two planes upstream
+    # (measured 7.6e-4 of its maximum; the outlet condition bends it slightly)
+    sig = L.field_stress().reshape(nz, n, n, 6)
+    shear_out, shear_up = sig[-1, ..., 4:6], sig[-3, ..., 4:6]
+    assert np.abs(shear_up).max() > 0.0
+    assert np.abs(shear_out - shear_up).max() < 3e-3 * np.abs(shear_up).max()
 
 
 def channel_wall_fit(orc, n, nz, nu, ylo, yhi, use_q=True, steps=3000):
@@ -664,6 +671,44 @@ def test_noise_uniform(orc):
     assert abs(vals.mean()) < 0.02
     assert orc.noise(3, 4, 5, 1) == orc.noise(3, 4, 5, 1)
     assert orc.noise(3, 4, 5, 1) != orc.noise(3, 4, 5, 2)
+
+
+def test_noise_depends_on_every_counter(orc):
+    """The draw for (seed, step, node, component) changes with each of the
+    four: streams that differ in one counter are uncorrelated and share no
+    value (24-bit draws coincide with probability 2^-24)."""
+    base = dict(seed=3, step=7, node=0, comp=0)
+    for key, other in (("seed", 4), ("step", 8), ("node", None), ("comp", 2)):
+        a, b = [], []
+        for k in range(600):
+            p = dict(base, node=k)
+            q = dict(p, **{key: other}) if other is not None else dict(p, node=k + 600)
+            a.append(orc.noise(p["seed"], p["step"], p["node"], p["comp"]))
+            b.append(orc.noise(q["seed"], q["step"], q["node"], q["comp"]))
+        a, b = np.array(a), np.array(b)
+        assert np.count_nonzero(a == b) <= 1, key
+        assert abs(np.corrcoef(a, b)[0, 1]) < 0.15, key
+
+
+def test_totals_compensated_on_an_ill_conditioned_sum(orc):
+    """Totals of 57 unit masses between +1e16 and -1e16: a plain running sum
+    loses every unit (half an ulp of 1e16 is 1), a compensated one stays
+    within Kahan's bound 2 eps sum|x| (about 4.4) of the exact 57."""
+    flags = np.ones((3, 4, 5), dtype=np.uint8)
+    flags[1, 1, 1] = 0
+    act = np.nonzero(flags.reshape(-1) != 0)[0]
+    f = np.zeros((flags.size, Q))
+    f[act, 13] = 1.0
+    f[act[0], 13], f[act[-1], 13] = 1e16, -1e16
+    L = orc.Lattice(flags, omega=1.0)
+    L.set_populations(f)
+    exact = math.fsum(f[act, 13])
+    bound = 2.0 * np.finfo(float).eps * np.abs(f[act, 13]).sum()
+    plain = 0.0
+    for v in f[act, 13]:
+        plain += v
+    assert exact == 57.0 and abs(plain - exact) > bound
+    assert abs(L.totals()[0] - exact) <= bound
 
 
 def test_totals_compensated(orc):
