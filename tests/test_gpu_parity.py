@@ -112,7 +112,7 @@ def test_noise_draws_bit_exact(orc, lbm):
     assert np.abs(u[inlet] - O.moments()[inlet, 1:]).max() < 1e-15
 
 
-def nozzle_cfg1():
+def nozzle_re500_setup():
     w = I.WORKLOADS["nozzle_re500_24x24x160"]
     nu = w["u_throat"] * w["d"] / w["Re"]
     bc = dict(profile="plug", u_in=I.inlet_mean_velocity(w))
@@ -120,9 +120,9 @@ def nozzle_cfg1():
 
 
 @pytest.fixture(scope="module")
-def cfg1_oracle(orc):
+def re500_oracle(orc):
     """The Re 500 laminar nozzle, 100 steps from rest, on the oracle."""
-    flags, nu, bc = nozzle_cfg1()
+    flags, nu, bc = nozzle_re500_setup()
     O = oracle_lattice(orc, flags, nu, **bc)
     O.init_equilibrium(1.0, [0.0, 0.0, 0.0])
     O.step(100)
@@ -130,9 +130,9 @@ def cfg1_oracle(orc):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
-def test_nozzle_re500_100_steps(lbm, cfg1_oracle, precision):
-    flags, O = cfg1_oracle
-    _, nu, bc = nozzle_cfg1()
+def test_nozzle_re500_100_steps(lbm, re500_oracle, precision):
+    flags, O = re500_oracle
+    _, nu, bc = nozzle_re500_setup()
     G = gpu_lattice(lbm, flags, precision, nu, **bc)
     G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
     G.step(100).sync()
@@ -212,7 +212,7 @@ def test_statistics_match_oracle_samples(orc, lbm):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16s"])
 def test_checkpoint_restore_bitwise(orc, lbm, precision):
-    flags, nu, bc = nozzle_cfg1()
+    flags, nu, bc = nozzle_re500_setup()
     A = gpu_lattice(lbm, flags, precision, nu, **bc)
     A.init_equilibrium(1.0, (0.0, 0.0, 0.0))
     A.stats_begin(1)
