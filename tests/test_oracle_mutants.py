@@ -126,6 +126,85 @@ MUTANTS = {
         "for (int k = 0; k < 6; ++k) sigma[b * 6 + k] = sigma[bf * 6 + k];",
         "for (int k = 0; k < 6; ++k) sigma[b * 6 + k] = 0.0;",
         [("test_square_duct_poiseuille_profile",)]),
+    "inlet_axis_offset": (
+        "radius measured from the cell corner instead of its centre",
+        "double rx = x + 0.5 - L->axis_x, ry = y + 0.5 - L->axis_y;", "double rx = x - L->axis_x, ry = y - L->axis_y;",
+        [("test_nee_boundary_nodes",)]),
+    "parabola_peak": (
+        "parabolic profile peaking at u0 instead of 2 u0 (Sec. 2.2 inlet profile)",
+        "speed = 2.0 * L->u_in * (1.0 - 4.0 * r2", "speed = L->u_in * (1.0 - 4.0 * r2",
+        [("test_nee_boundary_nodes",)]),
+    "noise_not_scaled_by_u0": (
+        "inlet perturbation not scaled by the mean inlet velocity",
+        "u[a] += L->noise_amp * L->u_in * orc_noise(L->seed, step, node, a);",
+        "u[a] += L->noise_amp * orc_noise(L->seed, step, node, a);",
+        [("test_nee_boundary_nodes",)]),
+    "noise_counter_packing": (
+        "node and component packed so that two pairs share a counter",
+        "h = orc_splitmix64((((uint64_t)node << 2) | (uint64_t)comp) + h);",
+        "h = orc_splitmix64((((uint64_t)node << 1) + (uint64_t)comp) + h);",
+        [("test_noise_depends_on_every_counter",)]),
+    "outlet_velocity_zero": (
+        "outlet velocity set to zero instead of extrapolated",
+        "for (int a = 0; a < 3; ++a) u_b[a] = u_f[a];", "for (int a = 0; a < 3; ++a) u_b[a] = 0.0;",
+        [("test_nee_boundary_nodes",), ("test_plug_flow_is_fixed_point",)]),
+    "inlet_direction": (
+        "inlet speed put on every axis instead of along the inward normal",
+        "u[a] = speed * n[a];", "u[a] = speed;",
+        [("test_nee_boundary_nodes",)]),
+    "nee_previous_partner": (
+        "NEE takes the partner's populations of the previous step",
+        "fout[b * ORC_Q + i] = feq_b[i] + (fout[bf * ORC_Q + i] - feq_f[i]);",
+        "fout[b * ORC_Q + i] = feq_b[i] + (fin[bf * ORC_Q + i] - feq_f[i]);",
+        [("test_nee_boundary_nodes",)]),
+    "nee_partner_not_unique": (
+        "a boundary node with several fluid axis neighbours accepted",
+        "return count == 1 ? found : -1;", "return count >= 1 ? found : -1;",
+        [("test_nee_partner_must_be_unique",)]),
+    "stress_component_pairs": (
+        "stress components xy and xz exchanged",
+        "static const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};",
+        "static const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 2, 1, 2};",
+        [("test_viscous_stress_shear_wave",)]),
+    "stress_viscosity": (
+        "viscosity theta0 tau instead of theta0 (tau - 1/2)",
+        "nu = ORC_THETA0 * (tau - 0.5);", "nu = ORC_THETA0 * tau;",
+        [("test_viscous_stress_shear_wave",)]),
+    "stress_from_post_collision": (
+        "stress taken from the post-collision instead of the gathered populations",
+        "        gather(L, fin, x, y, z, f);\n        orc_viscous_stress(f, L->omega, sigma + b * 6);",
+        "        for (int i = 0; i < ORC_Q; ++i) f[i] = fin[b * ORC_Q + i];\n"
+        "        orc_viscous_stress(f, L->omega, sigma + b * 6);",
+        [("test_viscous_stress_shear_wave",)]),
+    "wall_distance_scale": (
+        "wall distances decoded in 1/255 instead of 1/256",
+        "const double q = L->wall_q[self * ORC_Q + i] / 256.0;", "const double q = L->wall_q[self * ORC_Q + i] / 255.0;",
+        [("test_interpolated_bounce_back_places_the_walls",)]),
+    "bouzidi_near_branch_missing": (
+        "the q < 1/2 branch of Bouzidi's interpolation never taken",
+        "if (q < 0.5) {", "if (q < 0.0) {",
+        [("test_interpolated_bounce_back_places_the_walls",)]),
+    "back_substitution_sign": (
+        "wrong sign in the back substitution",
+        "for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * b[j];", "for (int j = k + 1; j < n; ++j) s += A[k * n + j] * b[j];",
+        [("test_gaussian_elimination_matches_lapack",)]),
+    "equilibrium_axis": (
+        "equilibrium coefficients built from u_x on every axis",
+        "for (int k = 0; k < n; ++k) a[m] *= u[idx[k]];", "for (int k = 0; k < n; ++k) a[m] *= u[0];",
+        [("test_equilibrium_closed_forms", 0)]),
+    "momentum_axis": (
+        "momentum summed with c_x on every axis",
+        "for (int a = 0; a < 3; ++a) j[a] += c[a] * f[i];", "for (int a = 0; a < 3; ++a) j[a] += c[0] * f[i];",
+        [("test_collision_conserves_mass_momentum", 0)]),
+    "raw_instead_of_central": (
+        "raw Hermite moments H_m(c) instead of central ones H_m(c - u)",
+        "double xi[3] = {c[0] - u[0], c[1] - u[1], c[2] - u[2]};",
+        "double xi[3] = {(double)c[0], (double)c[1], (double)c[2]};",
+        [("test_central_equilibrium_moments_vanish", 0)]),
+    "totals_momentum": (
+        "total momentum summed without the velocities",
+        "for (int a = 0; a < 3; ++a) v[1 + a] += c[a] * fi;", "for (int a = 0; a < 3; ++a) v[1 + a] += fi;",
+        [("test_totals_compensated",)]),
     "totals_uncompensated": (
         "compensation dropped from the FP64 totals",
         "comp[k] = (t - s[k]) - y;", "comp[k] = 0.0;",

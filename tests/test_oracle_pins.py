@@ -651,6 +651,27 @@ def test_nee_boundary_nodes(orc):
                 assert abs(got[0] - rb) < 1e-14 and np.allclose(got[1:], ub, atol=1e-14)
 
 
+def test_nee_partner_must_be_unique(orc):
+    """An inlet node's interior partner is its one FLUID axis neighbour: a
+    node with two or with none has no partner, and the step refuses the flag
+    field."""
+    flags = np.ones((4, 3, 3), dtype=np.uint8)
+    flags[0, 1, 1] = 2          # inlet whose +x, -x, +y, -y and +z neighbours are all fluid
+    L = orc.Lattice(flags, omega=1.0, periodic=3)
+    assert L.nee_neighbour(1, 1, 0)[0] == -1
+    L.init_equilibrium(1.0, [0.0, 0.0, 0.0])
+    with pytest.raises(RuntimeError):
+        L.step(1)
+    flags = np.zeros((4, 3, 3), dtype=np.uint8)
+    flags[0, 1, 1] = 2          # inlet without any fluid neighbour
+    flags[2:, 1, 1] = 1
+    L = orc.Lattice(flags, omega=1.0)
+    assert L.nee_neighbour(1, 1, 0)[0] == -1
+    duct = duct_flags(4, 8)     # every inlet node of a duct has exactly one
+    L = orc.Lattice(duct, omega=1.0, periodic=3)
+    assert all(L.nee_neighbour(x, y, 0)[0] == x + 4 * (y + 4) for x in range(4) for y in range(4))
+
+
 # -------------------------------------------------------------- noise, totals
 
 def test_splitmix64_reference_outputs(orc):
@@ -688,6 +709,14 @@ def test_noise_depends_on_every_counter(orc):
         a, b = np.array(a), np.array(b)
         assert np.count_nonzero(a == b) <= 1, key
         assert abs(np.corrcoef(a, b)[0, 1]) < 0.15, key
+    # distinct (node, component) pairs give independent draws: among 3000
+    # 24-bit draws about 0.27 coincide by chance (birthday bound), while two
+    # pairs that share a counter value would repeat a draw every time
+    repeats = 0
+    for seed, step in ((1, 1), (2, 5), (11, 7)):
+        grid = np.array([orc.noise(seed, step, node, comp) for node in range(1000) for comp in range(3)])
+        repeats += grid.size - np.unique(grid).size
+    assert repeats <= 6
 
 
 def test_totals_compensated_on_an_ill_conditioned_sum(orc):
