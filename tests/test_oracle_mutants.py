@@ -205,6 +205,47 @@ MUTANTS = {
         "total momentum summed without the velocities",
         "for (int a = 0; a < 3; ++a) v[1 + a] += c[a] * fi;", "for (int a = 0; a < 3; ++a) v[1 + a] += fi;",
         [("test_totals_compensated",)]),
+    "hermite_pairs_any_index": (
+        "Hermite delta terms paired across different axes",
+        "        if (idx[k] != idx[0]) continue;\n", "        (void)0;\n",
+        [("test_hermite_matches_printed_forms",), ("test_central_equilibrium_moments_vanish", 0)]),
+    "moment_index_degrees": (
+        "x and y degrees of the moment multi-index exchanged",
+        "    deg[0] = m % 3;\n    deg[1] = (m / 3) % 3;", "    deg[1] = m % 3;\n    deg[0] = (m / 3) % 3;",
+        [("test_central_equilibrium_moments_vanish", 0)]),
+    "velocity_index": (
+        "y and z components of the stencil velocity exchanged",
+        "    c[1] = (i / 3) % 3 - 1;\n    c[2] = i / 9 - 1;", "    c[2] = (i / 3) % 3 - 1;\n    c[1] = i / 9 - 1;",
+        [("test_central_equilibrium_moments_vanish", 0)]),
+    "theta0_perturbed": (
+        "stencil temperature off by 1e-9",
+        "#define ORC_THETA0 (1.0 / 3.0)", "#define ORC_THETA0 (1.0 / 3.0 + 1e-9)",
+        [("test_central_equilibrium_moments_vanish", 0)]),
+    "relaxation_sign": (
+        "relaxation applied away from equilibrium",
+        "rhs[m] = rate_of(m, omega, ghost, omega_cons) * s;", "rhs[m] = -rate_of(m, omega, ghost, omega_cons) * s;",
+        [("test_collision_reduces_to_bgk", 0.6)]),
+    "relaxation_without_f": (
+        "collision relaxes f^eq instead of f^eq - f",
+        "for (int i = 0; i < ORC_Q; ++i) d[i] = feq[i] - f[i];", "for (int i = 0; i < ORC_Q; ++i) d[i] = feq[i];",
+        [("test_collision_conserves_mass_momentum", 0)]),
+    "closed_faces_wrap": (
+        "non-periodic faces treated as periodic",
+        "    return periodic ? 1 : 0;", "    return 1;",
+        [("test_streaming_pull_and_bounce_back", 0), ("test_nee_partner_must_be_unique",)]),
+    "ramp_starts_late": (
+        "start-up ramp one step late",
+        "double s = (double)step / (double)L->ramp;", "double s = (double)(step - 1) / (double)L->ramp;",
+        [("test_inlet_start_up_ramp",)]),
+    "node_moments_not_read_back": (
+        "field readback leaves out the inlet/outlet nodes",
+        "        if (L->flags[b] == ORC_SOLID) { for (int a = 0; a < 4; ++a) mom[b * 4 + a] = 0.0; continue; }",
+        "        if (L->flags[b] != ORC_FLUID) { for (int a = 0; a < 4; ++a) mom[b * 4 + a] = 0.0; continue; }",
+        [("test_nee_boundary_nodes",)]),
+    "node_moments_recorded_wrong": (
+        "the step records the partner's density at an inlet/outlet node",
+        "        m[b * 4] = rho_b;", "        m[b * 4] = rho_f;",
+        [("test_nee_boundary_nodes",)]),
     "totals_uncompensated": (
         "compensation dropped from the FP64 totals",
         "comp[k] = (t - s[k]) - y;", "comp[k] = 0.0;",

@@ -628,7 +628,8 @@ def test_nee_boundary_nodes(orc):
     L.init_equilibrium(1.0 + 0.01 * g.uniform(-1, 1, n), 0.03 * g.uniform(-1, 1, (n, 3)))
     L.f *= 1.0 + 0.02 * g.uniform(-1, 1, L.f.shape)
     L.step(1)
-    mom = L.last_moments
+    mom = L.last_moments          # recorded by the step (the statistics use these)
+    field = L.moments()           # read back from the populations
     nx = ny = 4
     for y in range(ny):
         for x in range(nx):
@@ -649,6 +650,8 @@ def test_nee_boundary_nodes(orc):
                 assert np.allclose(L.f[b], expect, atol=1e-15)
                 got = orc.moments(L.f[b])
                 assert abs(got[0] - rb) < 1e-14 and np.allclose(got[1:], ub, atol=1e-14)
+                for m in (mom[b], field[b]):
+                    assert abs(m[0] - rb) < 1e-14 and np.allclose(m[1:], ub, atol=1e-14)
 
 
 def test_nee_partner_must_be_unique(orc):
