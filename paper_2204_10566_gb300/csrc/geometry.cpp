@@ -221,19 +221,65 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
             if (flags[bx] != LBM_FLUID || seen[bx]++) return "chunk lane is not a unique fluid cell";
         }
     }
-    // pulls of every fluid cell land on stored slots: an active cell's, or a
-    // non-active slot that marks the pulled array as read (never filled)
+    // Every position the step reads or writes owns its slot: the active
+    // cells, their periodic-x copies, and the ghost position of every wall
+    // link (x - c_i in the pulled row; rows wrap on periodic y / z faces).
+    // Two positions sharing a slot (overlapping row ranges, a missing copy)
+    // would overwrite each other.
+    const bool px = periodic & LBM_PERIODIC_X, py = periodic & LBM_PERIODIC_Y, pz = periodic & LBM_PERIODIC_Z;
+    std::vector<int32_t> slot_of_box((size_t)nx * ny * nz, -1);
+    std::vector<int64_t> owner((size_t)ns, -1);
+    const int64_t width = (int64_t)nx + 2;  // positions -1 .. nx of a row
+    auto row_e = [&](int y, int z) -> int64_t { return (int64_t)(y + 1) + (int64_t)ix.ny_e * (z + 1); };
+    auto claim = [&](int64_t row, int x, int64_t s) -> bool {
+        if (s < 0 || s >= ns) return false;
+        const int64_t key = row * width + (x + 1);
+        int64_t &o = owner[(size_t)s];
+        if (o < 0) o = key;
+        return o == key;
+    };
+    for (int64_t k = 0; k < ix.n_active; ++k) {
+        const int64_t bx = ix.box_of_active[k];
+        const int x = (int)(bx % nx), y = (int)((bx / nx) % ny), z = (int)(bx / ((int64_t)nx * ny));
+        const int32_t *nb = &ix.row_nb[(size_t)row_e(y, z) * ROW_RECORD_INTS];
+        slot_of_box[(size_t)bx] = ix.slot_of_active[k];
+        if (!claim(row_e(y, z), x, ix.slot_of_active[k])) return "two positions share the slot of an active cell";
+        if (px && x == nx - 1 && !claim(row_e(y, z), -1, (int64_t)nb[4] - 1)) return "periodic copy slot";
+        if (px && x == 0 && !claim(row_e(y, z), nx, (int64_t)nb[4] + nx)) return "periodic copy slot";
+    }
+    // pulls of every fluid cell land on stored slots: exactly the slot of an
+    // active source inside the box, else a non-active slot of the pulled
+    // position that marks the pulled array as read (never filled)
     for (int64_t k = 0; k < ix.n_active; ++k) {
         const int64_t bx = ix.box_of_active[k];
         if (flags[bx] != LBM_FLUID) continue;
         const int x = (int)(bx % nx), y = (int)((bx / nx) % ny), z = (int)(bx / ((int64_t)nx * ny));
-        const int32_t *nb = &ix.row_nb[(size_t)((y + 1) + (int64_t)ix.ny_e * (z + 1)) * ROW_RECORD_INTS];
+        const int32_t *nb = &ix.row_nb[(size_t)row_e(y, z) * ROW_RECORD_INTS];
         if (nb[4] + x != ix.slot_of_active[k]) return "slot of an active cell";
         for (int i = 0; i < 27; ++i) {
-            const int64_t s = (int64_t)nb[i / 3] + x - (i % 3 - 1);
+            const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+            const int64_t s = (int64_t)nb[i / 3] + x - cx;
             if (s < 0 || s >= ns) return "pull slot outside the buffer";
             const uint32_t m = ix.mask[(size_t)s];
             if (((m >> TYPE_SHIFT) & 3u) == TYPE_PAD && !((m >> i) & 1u)) return "pulled slot not marked as read";
+            int xs = x - cx, ys = y - cy, zs = z - cz;
+            bool outside = false, wrapped_x = false;
+            if (xs < 0 || xs >= nx) {
+                if (px) { xs = (xs + nx) % nx; wrapped_x = true; } else outside = true;
+            }
+            if (ys < 0 || ys >= ny) { if (py) ys = (ys + ny) % ny; else outside = true; }
+            if (zs < 0 || zs >= nz) { if (pz) zs = (zs + nz) % nz; else outside = true; }
+            if (!outside && !wrapped_x) {
+                const int32_t own = slot_of_box[(size_t)(xs + (int64_t)nx * (ys + (int64_t)ny * zs))];
+                if (own >= 0) {
+                    if (s != own) return "pull of an active source misses its slot";
+                    continue;
+                }
+            }
+            // ghost of a wall link, or a periodic-x copy: the pulled row (wrapped
+            // on periodic y / z faces) at x - cx
+            if (!claim(row_e(py ? ys : y - cy, pz ? zs : z - cz), x - cx, s))
+                return "two positions share a ghost or copy slot";
         }
     }
     for (int64_t b = 0; b < (int64_t)seen.size(); ++b)
@@ -254,7 +300,7 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     }
     for (const int4 &n : ix.bnodes)
         if (n.z < 0 || n.z >= ns || ix.row_nb[(size_t)n.y * ROW_RECORD_INTS + 4] + n.x != n.z) return "boundary node";
-    (void)periodic;
+
     return "";
 }
 
