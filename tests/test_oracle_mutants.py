@@ -289,3 +289,31 @@ def test_pins_catch_planted_mistake(mutant_dir, name):
     finally:
         oracle._lib = saved
     assert caught, "no pin caught: " + what
+
+
+# Mistakes in the oracle's Python side: the per-step sampled time averages.
+def _sampled_after_step(self, n):
+    """step_sampled with the stress sampled after the step instead of before it."""
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    acc = dict(u=np.zeros((self.ncell, 3)), uu=np.zeros((self.ncell, 6)), sigma=np.zeros((self.ncell, 6)),
+               rho=np.zeros(self.ncell))
+    for _ in range(n):
+        self.step(1)
+        acc["sigma"] += self.field_stress()
+        m = self.last_moments
+        acc["u"] += m[:, 1:4]
+        acc["uu"] += np.stack([m[:, 1 + a] * m[:, 1 + b] for a, b in pairs], axis=1)
+        acc["rho"] += m[:, 0]
+    return {k: v / n for k, v in acc.items()}
+
+
+def _sampled_one_too_many(self, n, _orig=oracle.Lattice.step_sampled):
+    """step_sampled dividing the sums by n + 1."""
+    return {k: v * n / (n + 1) for k, v in _orig(self, n).items()}
+
+
+@pytest.mark.parametrize("broken", [_sampled_after_step, _sampled_one_too_many], ids=lambda f: f.__name__)
+def test_pins_catch_planted_mistake_in_sampling(monkeypatch, broken):
+    monkeypatch.setattr(oracle.Lattice, "step_sampled", broken)
+    with pytest.raises(AssertionError):
+        pins.test_sampled_time_averages_of_a_decaying_wave(oracle)

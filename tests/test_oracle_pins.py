@@ -477,6 +477,39 @@ def test_viscous_stress_longitudinal_wave(orc):
     assert o < 1e-6
 
 
+def test_sampled_time_averages_of_a_decaying_wave(orc):
+    """Per-step sampled time averages (Sec. 2.2 mean / fluctuation
+    decomposition) of a decaying shear wave u_x = A sin(k y) lambda^t,
+    lambda = exp(-nu k^2): over n steps the mean of u is A times the mean
+    of lambda^t for t = 1..n (sampled after each step), the mean of u_x^2
+    the same with lambda^2t, and the mean stress sigma_xy that of the
+    pre-step states, t = 0..n-1; rho averages to 1 and every other
+    component to 0 (the diagonal stresses to second order in u)."""
+    n, nu, steps = 32, 0.02, 20
+    k = 2 * np.pi / n
+    c = np.arange(n) + 0.5
+    s, co = np.sin(k * c), np.cos(k * c)
+    L = orc.Lattice(np.ones((1, n, 2), dtype=np.uint8), omega=omega_of_nu(nu), periodic=7)
+    u = np.zeros((1, n, 2, 3))
+    u[0, :, :, 0] = 0.01 * s[:, None]
+    L.init_equilibrium(1.0, u.reshape(-1, 3))
+    L.step(50)
+    A0 = (L.moments().reshape(n, 2, 4)[:, 0, 1] * s).sum() / (s * s).sum()
+    S0 = (L.field_stress().reshape(n, 2, 6)[:, 0, 3] * co).sum() / (co * co).sum()
+    lam = np.exp(-nu * k * k)
+    t = np.arange(1, steps + 1)
+    avg = L.step_sampled(steps)
+    um = avg["u"].reshape(n, 2, 3)[:, 0]
+    uu = avg["uu"].reshape(n, 2, 6)[:, 0]
+    sg = avg["sigma"].reshape(n, 2, 6)[:, 0]
+    assert abs((um[:, 0] * s).sum() / (s * s).sum() / (A0 * np.mean(lam ** t)) - 1.0) < 1e-4
+    assert abs((uu[:, 0] * s * s).sum() / (s ** 4).sum() / (A0 ** 2 * np.mean(lam ** (2 * t))) - 1.0) < 2e-4
+    assert abs((sg[:, 3] * co).sum() / (co * co).sum() / (S0 * np.mean(lam ** (t - 1))) - 1.0) < 1e-4
+    assert np.abs(avg["rho"] - 1.0).max() < 1e-6
+    assert np.abs(um[:, 1:]).max() < 1e-9 and np.abs(uu[:, 1:]).max() < 1e-9
+    assert np.abs(sg[:, [0, 1, 2, 4, 5]]).max() < 1e-3 * abs(S0)
+
+
 # --------------------------------------------------------------- inlet/outlet
 
 def duct_flags(n, nz):
