@@ -199,6 +199,34 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p);
  * failed check ("" on success).  Any of nu, omega, why may be NULL. */
 lbm_status lbm_params_check(const lbm_params *p, double *nu, double *omega, const char **why);
 
+/* A run given in physical units (SI), as Sec. 2.2 states the problem. */
+typedef struct {
+    double Re;       /* Reynolds number on the throat, Re = rho u_thr d_thr / mu */
+    double d_thr;    /* throat diameter (m) */
+    double rho;      /* fluid density (kg / m^3) */
+    double mu;       /* dynamic viscosity (Pa s) */
+    double delta_r;  /* grid spacing (m) */
+    double delta_t;  /* time step (s); <= 0: the CFL rule below gives it */
+    double CFL;      /* used when delta_t <= 0: CFL = 2 u_thr delta_t / delta_r (Sec. 2.2) */
+} lbm_physical;
+
+/* Lattice parameters of a physical run (host only, no device needed), from
+ * the relations of Sec. 2.2: the throat mean velocity
+ * u_thr = mu Re / (rho d_thr); the time step, when not given, of the CFL rule
+ * delta_t = rho d_thr delta_r CFL / (2 mu Re); and in cells and steps the
+ * characteristic length L_char = d_thr / delta_r, velocity
+ * u_char = u_thr delta_t / delta_r and viscosity nu = mu delta_t / (rho delta_r^2),
+ * so that omega = 1/(3 nu + 1/2) equals delta_t / tau with the relaxation time
+ * tau = mu / (rho theta0) + delta_t / 2 of Sec. 2.1.  On LBM_OK it sets
+ * p->Re, p->u_char and p->L_char, and p->nu = 0 (nu then follows from Re),
+ * leaving the other fields of p as they were (fill it with
+ * lbm_params_default first); out (may be NULL) receives L_char, u_char, nu,
+ * CFL and delta_t (s).  The result must pass lbm_params_check (u_char below
+ * the lattice sound speed, 0 < omega < 2); otherwise p is unchanged, out is
+ * zero and the call returns LBM_ERR_ARG.  *why (may be NULL) receives "" or a
+ * static string naming the failed check. */
+lbm_status lbm_params_from_physical(const lbm_physical *ph, lbm_params *p, double out[5], const char **why);
+
 /* The relaxation rate omega in use. */
 lbm_status lbm_get_omega(lbm_ctx *ctx, double *omega);
 
@@ -308,13 +336,18 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes);
  *   stream: cudaStream_t (NULL: default stream); the call only enqueues work.
  * The per-block partial sums live in one static device array (256 KB) that
  * every GPU which loads the library holds until the process exits.  The first
- * call on a device looks up that array's device address (with the device
- * current); make that first call before any stream capture.  All calls share
+ * call in a CUDA context (per device, and again after a context is re-created,
+ * e.g. after cudaDeviceReset) looks up that array's device address with the
+ * device current; host threads may call concurrently, the lookup is guarded.
+ * Make that first call before any stream capture: if it finds `stream`
+ * capturing it returns LBM_ERR_STATE and enqueues nothing.  All calls share
  * the array: calls whose work overlaps on the GPU (e.g. on two streams) race
  * and must be serialised by the caller.  Every call overwrites all the
- * partials it reads, so nothing needs clearing between calls.
+ * partials it reads, so nothing needs clearing between calls.  The returned
+ * status covers this call's own launches only.
  * Errors: LBM_ERR_ARG (NULL pointer, n out of range, stride < n, bad
- * precision or scale), LBM_ERR_CUDA. */
+ * precision or scale), LBM_ERR_STATE (first call in a context inside a stream
+ * capture), LBM_ERR_CUDA. */
 lbm_status lbm_totals_noalloc(const void *f, int32_t precision, float fp16_scale, int64_t n, int64_t stride,
                               double *out, void *stream);
 
@@ -364,15 +397,35 @@ lbm_status lbm_server_destroy(lbm_server *s);
 const char *lbm_server_last_error(const lbm_server *s);
 
 /* Queue a request; *id receives its handle.  The flag field is checked and
- * its sparse index built in a background host thread.  Errors: LBM_ERR_ARG
- * (bad request), LBM_ERR_OOM (its lattice can never fit the budget). */
+ * its sparse index built in a background host thread.  The server's
+ * multi-lattice kernels address populations with 32-bit offsets, so a
+ * lattice needs fewer than 2^32 / 27 storage slots (active cells plus row
+ * padding and bounce-back ghost slots, about 159 M); larger ones run with
+ * lbm_step.  Errors: LBM_ERR_ARG (bad request; more active cells than that
+ * limit), LBM_ERR_OOM (its lattice can never fit the budget).  A request
+ * whose index turns out to need too many slots, or whose exact footprint
+ * exceeds the budget, ends FAILED at a later tick. */
 lbm_status lbm_server_submit(lbm_server *s, const lbm_request *req, int64_t *id);
+
+/* Every check lbm_server_submit and the later admission apply to a request,
+ * on the host, without a server or a device: the checks of submit, the
+ * sparse index build with the 32-bit slot limit, and the exact device
+ * footprint against budget_bytes.  out (may be NULL) receives: active cells,
+ * storage slots, device footprint in bytes, inlet/outlet nodes.  *why (may
+ * be NULL) receives "" or the reason of a refusal (valid until the next
+ * call of this function on the same thread).
+ * Errors: LBM_ERR_ARG, LBM_ERR_OOM (as lbm_server_submit). */
+lbm_status lbm_server_check_request(const lbm_request *req, int64_t budget_bytes, int64_t out[4],
+                                    const char **why);
 
 /* One scheduling tick: admit queued requests whose index is built (in
  * submission order, while a slot is free and the footprint fits), advance
  * every resident lattice by up to steps_per_tick steps, retire the finished
- * ones (read back rho, u; free their memory).  Blocks until the tick's work
- * is done.  Outputs (may be NULL): resident lattices, queued requests. */
+ * ones (read back rho, u; free their memory).  The last step a lattice takes
+ * in a tick is its health check: a lattice with a non-finite density or
+ * velocity is evicted (its memory freed) and ends FAILED with
+ * LBM_ERR_UNSTABLE; the others are not affected.  Blocks until the tick's
+ * work is done.  Outputs (may be NULL): resident lattices, queued requests. */
 lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued);
 
 /* State (LBM_REQ_*) and steps done of a request. */
@@ -382,9 +435,15 @@ lbm_status lbm_server_poll(lbm_server *s, int64_t id, int32_t *state, int64_t *s
  * LBM_ERR_STATE before). */
 lbm_status lbm_server_cells(lbm_server *s, int64_t id, int64_t *active_cells);
 
-/* Final density rho[n] and velocity u[n][3] of a finished request, in the
- * active order of its flag field; releases the stored result.
- * Errors: LBM_ERR_STATE if not finished. */
+/* Final density rho[n] and velocity u[n][3] of a finished (DONE) request,
+ * in the active order of its flag field.  Called on any terminal request
+ * (DONE, FAILED, CANCELLED) it releases everything the server keeps for it,
+ * and the id is no longer valid afterwards; a FAILED request returns the
+ * status it failed with (LBM_ERR_UNSTABLE after a health check, LBM_ERR_ARG
+ * for a bad flag field or too many slots, LBM_ERR_OOM for a footprint above
+ * the budget, LBM_ERR_CUDA) and a CANCELLED one LBM_ERR_STATE, with the
+ * reason in lbm_server_last_error.
+ * Errors: LBM_ERR_STATE if still queued or running (the request is kept). */
 lbm_status lbm_server_result(lbm_server *s, int64_t id, double *rho, double *u);
 
 /* Cancel a queued or running request (its memory is freed at the next tick). */

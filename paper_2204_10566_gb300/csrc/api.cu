@@ -362,6 +362,7 @@ lbm_status lbm_destroy(lbm_ctx *c) {
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, int64_t n) {
+    const TraceRange trace("lbm_set_wall_q");
     lbm_status st = need(c, true, false, false);
     if (st) return st;
     if (n < 0 || (n > 0 && (!cells || !q))) return fail(c, LBM_ERR_ARG, "bad wall-distance arrays");
@@ -452,6 +453,7 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
 }
 
 lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
+    const TraceRange trace("lbm_set_geometry");
     if (!c) return LBM_ERR_ARG;
     if (!flags) return fail(c, LBM_ERR_ARG, "flags is NULL");
     HostIndex idx;
@@ -573,6 +575,41 @@ lbm_status lbm_params_check(const lbm_params *p, double *nu_out, double *omega_o
     }
     if (nu_out) *nu_out = st == LBM_OK ? nu : 0.0;
     if (omega_out) *omega_out = st == LBM_OK ? omega : 0.0;
+    if (why) *why = msg;
+    return st;
+}
+
+lbm_status lbm_params_from_physical(const lbm_physical *ph, lbm_params *p, double out[5], const char **why) {
+    const char *msg = "";
+    lbm_status st = LBM_ERR_ARG;
+    double lu[5] = {0, 0, 0, 0, 0};
+    if (!ph || !p) {
+        msg = "physical description or params is NULL";
+    } else if (!(ph->Re > 0.0) || !(ph->d_thr > 0.0) || !(ph->rho > 0.0) || !(ph->mu > 0.0) || !(ph->delta_r > 0.0)) {
+        msg = "Re, d_thr, rho, mu and delta_r must be > 0";
+    } else if (!(ph->delta_t > 0.0) && !(ph->CFL > 0.0)) {
+        msg = "give delta_t > 0 or CFL > 0";
+    } else {
+        // throat mean velocity from the throat Reynolds number Re = rho u_thr d_thr / mu (Sec. 2.2)
+        const double u_thr = ph->mu * ph->Re / (ph->rho * ph->d_thr);
+        // time step of the CFL rule CFL = 2 u_thr dt / dr (Sec. 2.2) when none is given
+        const double dt = ph->delta_t > 0.0 ? ph->delta_t
+                                            : ph->rho * ph->d_thr * ph->delta_r * ph->CFL / (2.0 * ph->mu * ph->Re);
+        lu[0] = ph->d_thr / ph->delta_r;                          // L_char: throat diameter in cells
+        lu[1] = u_thr * dt / ph->delta_r;                         // u_char: throat velocity in cells per step
+        lu[2] = ph->mu * dt / (ph->rho * ph->delta_r * ph->delta_r);  // nu in lattice units
+        lu[3] = 2.0 * lu[1];                                      // CFL of the throat mean velocity
+        lu[4] = dt;
+        lbm_params q = *p;
+        q.nu = 0.0;  // derived from Re = u_char L_char / nu
+        q.Re = ph->Re;
+        q.u_char = lu[1];
+        q.L_char = lu[0];
+        st = lbm_params_check(&q, nullptr, nullptr, &msg);
+        if (st == LBM_OK) *p = q;
+    }
+    if (out)
+        for (int k = 0; k < 5; ++k) out[k] = st == LBM_OK ? lu[k] : 0.0;
     if (why) *why = msg;
     return st;
 }
@@ -702,6 +739,7 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f, int32_t layout) {
 }
 
 lbm_status lbm_step(lbm_ctx *c, int64_t n) {
+    const TraceRange trace("lbm_step");
     lbm_status st = need(c, true, true, true);
     if (st) return st;
     if (n < 0) return fail(c, LBM_ERR_ARG, "negative step count");
@@ -729,6 +767,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
 }
 
 lbm_status lbm_sync(lbm_ctx *c) {
+    const TraceRange trace("lbm_sync");
     if (!c) return LBM_ERR_ARG;
     DeviceGuard g(c->desc.device);
     CK(cudaStreamSynchronize(c->stream), "sync");
@@ -759,6 +798,7 @@ lbm_status lbm_set_check_every(lbm_ctx *c, int64_t k) {
 }
 
 lbm_status lbm_get_moments(lbm_ctx *c, double *rho, double *u, int32_t layout) {
+    const TraceRange trace("lbm_get_moments");
     lbm_status st = need(c, true, false, true);
     if (st) return st;
     if ((!rho && !u) || (layout != LBM_LAYOUT_ACTIVE && layout != LBM_LAYOUT_BOX))
@@ -787,6 +827,7 @@ lbm_status lbm_get_moments(lbm_ctx *c, double *rho, double *u, int32_t layout) {
 }
 
 lbm_status lbm_get_totals(lbm_ctx *c, double *mass, double mom[3]) {
+    const TraceRange trace("lbm_get_totals");
     lbm_status st = need(c, true, false, true);
     if (st) return st;
     DeviceGuard g(c->desc.device);

@@ -27,7 +27,8 @@ static inline int64_t box_index(int x, int y, int z, int nx, int ny) {
     return (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
 }
 
-std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out) {
+std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out,
+                        int64_t max_slots) {
     const int64_t ncell = (int64_t)nx * ny * nz;
     for (int64_t b = 0; b < ncell; ++b)
         if (flags[b] > LBM_OUTLET) {
@@ -102,6 +103,12 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
         if (next > (int64_t)INT32_MAX / 2) return "lattice too large for 32-bit slot indices";
     }
     out.nslots = (next + 63) & ~(int64_t)63;
+    if (max_slots > 0 && out.nslots > max_slots) {  // refused before the per-slot arrays are allocated
+        char msg[192];
+        snprintf(msg, sizeof msg, "lattice needs %lld storage slots, more than the limit of %lld",
+                 (long long)out.nslots, (long long)max_slots);
+        return msg;
+    }
     out.mask.assign((size_t)out.nslots, (uint32_t)TYPE_PAD << TYPE_SHIFT);
     out.row_nb.assign((size_t)nrows * ROW_RECORD_INTS, 0);
     for (int z = 0; z < nz; ++z)

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -11,6 +12,16 @@
 #include "../../include/lbm.h"
 
 namespace lbm {
+
+// NVTX range over a host call (a no-op unless a profiler is attached): the
+// step loop, the reductions, index building and the server's ticks show up
+// by name on an Nsight timeline.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Cells per work chunk: a chunk is CHUNK consecutive x positions of one row
 // (fixed y, z).  Every row's storage starts and ends on a CHUNK boundary so
@@ -170,8 +181,11 @@ struct HostIndex {
 inline int64_t buffer_margin(int nx) { return ((int64_t)nx + 64 + 63) & ~(int64_t)63; }
 constexpr int64_t MASK_MARGIN = 64;
 
-// Returns "" on success, else a description of the inconsistency.
-std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out);
+// Returns "" on success, else a description of the inconsistency.  With
+// max_slots > 0, a lattice needing more storage slots is refused before its
+// per-slot arrays are allocated.
+std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out,
+                        int64_t max_slots = 0);
 // Independent check of the index invariants the kernels rely on ("" if all hold).
 std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, int ny, int nz, int periodic);
 

@@ -66,6 +66,9 @@ __device__ __forceinline__ int find_domain(const GroupTable *tab, int tile) {
 
 // Step k of the tick for the tile's lattice: copy its arguments to shared
 // memory, swap the buffers on odd steps, set the step number (inlet noise).
+// The lattice's last step of the tick is its health check: every cell then
+// computes its non-finite flag (STEP_REDUCE), and a.status points at the
+// lattice's word of the server's health-flag array.
 __device__ __forceinline__ bool load_domain(const DomainEntry &e, int k, StepArgs &sa) {
     if (k >= e.steps) return false;
     for (int w = threadIdx.x; w < (int)(sizeof(StepArgs) / 16); w += blockDim.x)
@@ -78,9 +81,17 @@ __device__ __forceinline__ bool load_domain(const DomainEntry &e, int k, StepArg
             sa.fout = const_cast<void *>(t);
         }
         sa.t_new = e.t_base + k + 1;
+        sa.flags = k == e.steps - 1 ? STEP_REDUCE : 0;
     }
     __syncthreads();
     return true;
+}
+
+// Health check of a tile on its lattice's check step: one atomic per warp
+// that saw a non-finite density or velocity (hv[5], set by record_cell).
+__device__ __forceinline__ void flag_non_finite(const StepArgs &sa, const double (&hv)[6]) {
+    if (!(sa.flags & STEP_REDUCE)) return;  // uniform over the block
+    if (__any_sync(0xffffffffu, hv[5] != 0.0) && (threadIdx.x & 31) == 0) atomicOr(sa.status, 1u);
 }
 
 template <int P>
@@ -96,7 +107,9 @@ __global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_multi_flu
         const DomainEntry &e = tab->d[s_dom];
         if (!load_domain(e, k, sa)) continue;  // uniform over the block
         const int chunk = (tile - e.tile_begin) * (STEP_THREADS / CHUNK) + threadIdx.x / CHUNK;
+        hv[5] = 0.0;
         if (chunk < sa.nchunks) fluid_cell<P, true, false>(sa, chunk, threadIdx.x % CHUNK, hv);
+        flag_non_finite(sa, hv);
     }
 }
 
@@ -113,7 +126,9 @@ __global__ void __launch_bounds__(STEP_THREADS) k_multi_boundary(const GroupTabl
         const DomainEntry &e = tab->d[s_dom];
         if (!load_domain(e, k, sa)) continue;
         const int node = (tile - e.btile_begin) * STEP_THREADS + threadIdx.x;
+        hv[5] = 0.0;
         if (node < sa.nbnodes) boundary_node<P, true, false>(sa, node, hv);
+        flag_non_finite(sa, hv);
     }
 }
 
@@ -128,6 +143,7 @@ struct Request {
     lbm_request req{};
     std::vector<uint8_t> flags;
     int state = LBM_REQ_QUEUED;
+    lbm_status fail_status = LBM_OK;  // why a FAILED request failed
     int64_t steps_done = 0;
     bool cancel = false;
     // built by a worker thread (guarded by the server mutex)
@@ -167,6 +183,9 @@ struct lbm_server {
     // device tables and the tick graph
     GroupTable *h_tab[NGROUPS] = {nullptr, nullptr};
     GroupTable *d_tab[NGROUPS] = {nullptr, nullptr};
+    // health flags, one word per (group, domain): cleared at the start of
+    // every tick, raised by the check step, copied back at its end
+    uint32_t *d_flags = nullptr, *h_flags = nullptr;
     cudaGraphExec_t exec = nullptr;
     int grid_fluid[NGROUPS] = {0, 0}, grid_bnd[NGROUPS] = {0, 0};
 };
@@ -176,6 +195,51 @@ namespace {
 lbm_status sfail(lbm_server *s, lbm_status st, const std::string &m) {
     if (s) s->err = m;
     return st;
+}
+
+// Device bytes a request holds while resident: the context's buffers plus
+// the readback staging of its moments.
+int64_t request_footprint(const lbm_request &q, const HostIndex &idx) {
+    lbm_desc d{};
+    d.nx = q.nx;
+    d.ny = q.ny;
+    d.nz = q.nz;
+    d.periodic = q.periodic;
+    d.precision = q.precision;
+    return ctx_footprint(d, idx) + idx.n_active * 32;
+}
+
+// The checks of lbm_server_submit that need no index (host only).  *active
+// receives the request's active cell count.
+lbm_status check_request(const lbm_request *q, int64_t budget_bytes, int64_t *active, const char **why) {
+    *active = 0;
+    auto bad = [why](lbm_status st, const char *m) {
+        *why = m;
+        return st;
+    };
+    if (!q || !q->flags) return bad(LBM_ERR_ARG, "NULL request or flags");
+    if (q->precision != LBM_FP32 && q->precision != LBM_FP16S)
+        return bad(LBM_ERR_ARG, "the server runs FP32 and FP16S lattices");
+    if (q->steps < 1 || q->nx < 1 || q->ny < 1 || q->nz < 1 || (q->periodic & ~7))
+        return bad(LBM_ERR_ARG, "bad lattice size, periodicity or step count");
+    const lbm_params &p = q->params;
+    if (p.omega3 != 1.0 || p.omega4 != 1.0 || p.omega5 != 1.0 || p.omega6 != 1.0)
+        return bad(LBM_ERR_ARG, "the server runs the default ghost rates only");
+    if (resolve_fp16_scale(q->fp16_scale) == 0.0f)
+        return bad(LBM_ERR_ARG, "the FP16 scale must be 0 (default) or a power of two");
+    if (lbm_params_check(&p, nullptr, nullptr, why) != LBM_OK) return LBM_ERR_ARG;  // lbm_set_params' checks
+    const int64_t ncell = (int64_t)q->nx * q->ny * q->nz;
+    int64_t n = 0;
+    for (int64_t b = 0; b < ncell; ++b) n += q->flags[b] != LBM_SOLID;
+    *active = n;
+    // every active cell has a slot: a lattice this large can never get 32-bit offsets
+    if (n > MAX_SLOTS_32)
+        return bad(LBM_ERR_ARG, "the lattice has more active cells than the server's 32-bit population "
+                                "offsets address (2^32 / 27 slots); run it with lbm_step");
+    if (2 * 27 * n * storage_size(q->precision) > budget_bytes)
+        return bad(LBM_ERR_OOM, "the lattice can never fit the server's memory budget");
+    *why = "";
+    return LBM_OK;
 }
 
 void worker_loop(lbm_server *s) {
@@ -188,16 +252,12 @@ void worker_loop(lbm_server *s) {
             r = s->build_queue.front();
             s->build_queue.pop_front();
         }
+        const TraceRange trace("lbm_server: index build");
         HostIndex idx;
         const lbm_request &q = r->req;
-        std::string e = build_index(r->flags.data(), q.nx, q.ny, q.nz, q.periodic, idx);
-        lbm_desc d{};
-        d.nx = q.nx;
-        d.ny = q.ny;
-        d.nz = q.nz;
-        d.periodic = q.periodic;
-        d.precision = q.precision;
-        const int64_t fp = e.empty() ? ctx_footprint(d, idx) + idx.n_active * 32 : 0;  // + readback staging
+        // the multi-lattice kernels address populations with 32-bit offsets
+        std::string e = build_index(r->flags.data(), q.nx, q.ny, q.nz, q.periodic, idx, MAX_SLOTS_32);
+        const int64_t fp = e.empty() ? request_footprint(q, idx) : 0;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             r->index_error = e;
@@ -226,12 +286,15 @@ lbm_status capture_tick(lbm_server *s) {
     if (e != cudaSuccess) return sfail(s, LBM_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
     for (int q = 0; q < NGROUPS; ++q)
         cudaMemcpyAsync(s->d_tab[q], s->h_tab[q], sizeof(GroupTable), cudaMemcpyHostToDevice, s->stream);
+    cudaMemsetAsync(s->d_flags, 0, NGROUPS * MAX_SLOTS * sizeof(uint32_t), s->stream);
     for (int k = 0; k < s->desc.steps_per_tick; ++k) {
         k_multi_fluid<1><<<s->grid_fluid[0], STEP_THREADS, 0, s->stream>>>(s->d_tab[0], k);
         k_multi_fluid<2><<<s->grid_fluid[1], STEP_THREADS, 0, s->stream>>>(s->d_tab[1], k);
         k_multi_boundary<1><<<s->grid_bnd[0], STEP_THREADS, 0, s->stream>>>(s->d_tab[0], k);
         k_multi_boundary<2><<<s->grid_bnd[1], STEP_THREADS, 0, s->stream>>>(s->d_tab[1], k);
     }
+    cudaMemcpyAsync(s->h_flags, s->d_flags, NGROUPS * MAX_SLOTS * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                    s->stream);
     e = cudaStreamEndCapture(s->stream, &g);
     if (e != cudaSuccess) return sfail(s, LBM_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&s->exec, g, 0);
@@ -278,6 +341,7 @@ lbm_status admit(lbm_server *s, Request *r) {
         if (c) lbm_destroy(c);
         drop_inputs(r);
         r->state = LBM_REQ_FAILED;
+        r->fail_status = st;
         return st;
     }
     r->ctx = c;
@@ -314,6 +378,8 @@ lbm_status lbm_server_create(const lbm_server_desc *desc, lbm_server **out) {
             if (s->h_tab[q]) cudaFreeHost(s->h_tab[q]);
             if (s->d_tab[q]) cudaFree(s->d_tab[q]);
         }
+        if (s->h_flags) cudaFreeHost(s->h_flags);
+        if (s->d_flags) cudaFree(s->d_flags);
         if (s->own_stream) cudaStreamDestroy(s->stream);
         cudaGetLastError();
         return st;
@@ -334,6 +400,15 @@ lbm_status lbm_server_create(const lbm_server_desc *desc, lbm_server **out) {
             s->d_tab[q] = nullptr;
             return undo(LBM_ERR_OOM);
         }
+    }
+    if (cudaMallocHost(&s->h_flags, NGROUPS * MAX_SLOTS * sizeof(uint32_t)) != cudaSuccess) {
+        s->h_flags = nullptr;
+        return undo(LBM_ERR_CUDA);
+    }
+    memset(s->h_flags, 0, NGROUPS * MAX_SLOTS * sizeof(uint32_t));
+    if (cudaMalloc(&s->d_flags, NGROUPS * MAX_SLOTS * sizeof(uint32_t)) != cudaSuccess) {
+        s->d_flags = nullptr;
+        return undo(LBM_ERR_OOM);
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, desc->device);
@@ -366,6 +441,8 @@ lbm_status lbm_server_destroy(lbm_server *s) {
         if (s->h_tab[q]) cudaFreeHost(s->h_tab[q]);
         if (s->d_tab[q]) cudaFree(s->d_tab[q]);
     }
+    if (s->h_flags) cudaFreeHost(s->h_flags);
+    if (s->d_flags) cudaFree(s->d_flags);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return LBM_OK;
@@ -375,25 +452,12 @@ const char *lbm_server_last_error(const lbm_server *s) { return s ? s->err.c_str
 
 lbm_status lbm_server_submit(lbm_server *s, const lbm_request *q, int64_t *id) {
     if (!s) return LBM_ERR_ARG;
-    if (!q || !id || !q->flags) return sfail(s, LBM_ERR_ARG, "NULL request, flags or id");
-    if (q->precision != LBM_FP32 && q->precision != LBM_FP16S)
-        return sfail(s, LBM_ERR_ARG, "the server runs FP32 and FP16S lattices");
-    if (q->steps < 1 || q->nx < 1 || q->ny < 1 || q->nz < 1 || (q->periodic & ~7))
-        return sfail(s, LBM_ERR_ARG, "bad lattice size, periodicity or step count");
-    const lbm_params &p = q->params;
-    if (p.omega3 != 1.0 || p.omega4 != 1.0 || p.omega5 != 1.0 || p.omega6 != 1.0)
-        return sfail(s, LBM_ERR_ARG, "the server runs the default ghost rates only");
-    if (resolve_fp16_scale(q->fp16_scale) == 0.0f)
-        return sfail(s, LBM_ERR_ARG, "the FP16 scale must be 0 (default) or a power of two");
-    {  // the checks of lbm_set_params, on the host
-        const char *why;
-        if (lbm_params_check(&p, nullptr, nullptr, &why) != LBM_OK) return sfail(s, LBM_ERR_ARG, why);
-    }
-    const int64_t ncell = (int64_t)q->nx * q->ny * q->nz;
+    if (!id) return sfail(s, LBM_ERR_ARG, "NULL id");
     int64_t active = 0;
-    for (int64_t b = 0; b < ncell; ++b) active += q->flags[b] != LBM_SOLID;
-    if (2 * 27 * active * storage_size(q->precision) > s->desc.budget_bytes)
-        return sfail(s, LBM_ERR_OOM, "the lattice can never fit the server's memory budget");
+    const char *why = "";
+    const lbm_status st = check_request(q, s->desc.budget_bytes, &active, &why);
+    if (st != LBM_OK) return sfail(s, st, why);
+    const int64_t ncell = (int64_t)q->nx * q->ny * q->nz;
     std::unique_ptr<Request> r(new Request());
     r->id = s->next_id++;
     r->req = *q;
@@ -412,6 +476,7 @@ lbm_status lbm_server_submit(lbm_server *s, const lbm_request *q, int64_t *id) {
 }
 
 lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
+    const TraceRange trace("lbm_server_tick");
     if (!s) return LBM_ERR_ARG;
     cudaSetDevice(s->desc.device);
     // retire cancelled lattices
@@ -448,6 +513,7 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
         if (!ready) break;  // admission keeps submission order: wait for this index
         if (!r->index_error.empty() || r->footprint > s->desc.budget_bytes) {
             r->state = LBM_REQ_FAILED;
+            r->fail_status = r->index_error.empty() ? LBM_ERR_OOM : LBM_ERR_ARG;
             drop_inputs(r);
             if (r->index_error.empty()) r->index_error = "footprint exceeds the memory budget";
             it = s->queue.erase(it);
@@ -472,12 +538,14 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
         s->h_tab[q]->n_btiles = 0;
     }
     const int K = s->desc.steps_per_tick;
-    std::vector<int> steps_now(s->resident.size());
+    std::vector<int> steps_now(s->resident.size()), flag_of(s->resident.size());
     for (size_t k = 0; k < s->resident.size(); ++k) {
         Request *r = s->reqs[s->resident[k]].get();
         GroupTable *tab = s->h_tab[r->group];
+        flag_of[k] = r->group * MAX_SLOTS + tab->n_domains;
         DomainEntry &e = tab->d[tab->n_domains++];
         ctx_step_args(r->ctx, &e.a);
+        e.a.status = s->d_flags + flag_of[k];  // the lattice's health flag
         e.t_base = r->steps_done;
         e.steps = (int32_t)std::min<int64_t>(K, r->req.steps - r->steps_done);
         steps_now[k] = e.steps;
@@ -490,8 +558,12 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
         lbm_status st = capture_tick(s);
         if (st != LBM_OK) return st;
     }
-    cudaError_t e = cudaGraphLaunch(s->exec, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaError_t e;
+    {
+        const TraceRange run("lbm_server_tick: graph");
+        e = cudaGraphLaunch(s->exec, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
     if (e != cudaSuccess) return sfail(s, LBM_ERR_CUDA, std::string("tick: ") + cudaGetErrorString(e));
     s->graph_launches += 1;
     s->ticks += 1;
@@ -502,11 +574,18 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
         ctx_advance(r->ctx, steps_now[k]);
         r->steps_done += steps_now[k];
         s->cell_updates += (double)r->n_active * steps_now[k];
-        if (r->steps_done >= r->req.steps) {
+        if (s->h_flags[flag_of[k]]) {  // the tick's health check saw a non-finite cell: evict
+            r->state = LBM_REQ_FAILED;
+            r->fail_status = LBM_ERR_UNSTABLE;
+            r->index_error = "non-finite density or velocity found by the health check at step " +
+                             std::to_string(r->steps_done);
+            release(s, r);
+        } else if (r->steps_done >= r->req.steps) {
             r->rho.assign((size_t)r->n_active, 0.0);
             r->u.assign((size_t)r->n_active * 3, 0.0);
             lbm_status st = lbm_get_moments(r->ctx, r->rho.data(), r->u.data(), LBM_LAYOUT_ACTIVE);
             r->state = st == LBM_OK ? LBM_REQ_DONE : LBM_REQ_FAILED;
+            r->fail_status = st;
             if (st != LBM_OK) r->index_error = lbm_last_error(r->ctx);
             release(s, r);
             s->finished += 1;
@@ -543,7 +622,21 @@ lbm_status lbm_server_result(lbm_server *s, int64_t id, double *rho, double *u) 
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return sfail(s, LBM_ERR_ARG, "unknown request id");
     Request *r = it->second.get();
-    if (r->state != LBM_REQ_DONE) return sfail(s, LBM_ERR_STATE, "request not finished");
+    if (r->state == LBM_REQ_QUEUED || r->state == LBM_REQ_RUNNING)
+        return sfail(s, LBM_ERR_STATE, "request not finished");
+    // a terminal request is released here, whatever its outcome (the worker
+    // threads are done with it: a request only leaves QUEUED once its index
+    // is built)
+    if (r->state == LBM_REQ_CANCELLED) {
+        s->reqs.erase(it);
+        return sfail(s, LBM_ERR_STATE, "request was cancelled");
+    }
+    if (r->state == LBM_REQ_FAILED) {
+        const lbm_status st = r->fail_status != LBM_OK ? r->fail_status : LBM_ERR_ARG;
+        const std::string msg = "request failed: " + r->index_error;
+        s->reqs.erase(it);
+        return sfail(s, st, msg);
+    }
     if (rho) memcpy(rho, r->rho.data(), r->rho.size() * 8);
     if (u) memcpy(u, r->u.data(), r->u.size() * 8);
     s->reqs.erase(it);
@@ -569,6 +662,37 @@ lbm_status lbm_server_info(lbm_server *s, double out[8]) {
     out[6] = s->finished;
     out[7] = (double)s->queue.size();
     return LBM_OK;
+}
+
+lbm_status lbm_server_check_request(const lbm_request *req, int64_t budget_bytes, int64_t out[4],
+                                    const char **why) {
+    static thread_local std::string msg;
+    const char *w = "";
+    int64_t active = 0;
+    if (out) out[0] = out[1] = out[2] = out[3] = 0;
+    lbm_status st = check_request(req, budget_bytes, &active, &w);
+    if (st == LBM_OK) {
+        HostIndex idx;
+        msg = build_index(req->flags, req->nx, req->ny, req->nz, req->periodic, idx, MAX_SLOTS_32);
+        if (!msg.empty()) {
+            st = LBM_ERR_ARG;
+            w = msg.c_str();
+        } else {
+            const int64_t fp = request_footprint(*req, idx);
+            if (out) {
+                out[0] = idx.n_active;
+                out[1] = idx.nslots;
+                out[2] = fp;
+                out[3] = (int64_t)idx.bnodes.size();
+            }
+            if (fp > budget_bytes) {
+                st = LBM_ERR_OOM;
+                w = "footprint exceeds the memory budget";
+            }
+        }
+    }
+    if (why) *why = w;
+    return st;
 }
 
 }  // extern "C"

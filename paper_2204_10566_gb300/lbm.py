@@ -58,6 +58,13 @@ class lbm_params(C.Structure):
     ]
 
 
+class lbm_physical(C.Structure):
+    _fields_ = [
+        ("Re", C.c_double), ("d_thr", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
+        ("delta_r", C.c_double), ("delta_t", C.c_double), ("CFL", C.c_double),
+    ]
+
+
 class lbm_server_desc(C.Structure):
     _fields_ = [
         ("device", C.c_int32), ("stream", C.c_void_p), ("allocator", lbm_allocator),
@@ -102,6 +109,8 @@ _SIGS = {
     "lbm_set_wall_q": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "lbm_set_params": (C.c_int, [C.c_void_p, C.POINTER(lbm_params)]),
     "lbm_params_check": (C.c_int, [C.POINTER(lbm_params), _dp, _dp, C.POINTER(C.c_char_p)]),
+    "lbm_params_from_physical": (C.c_int, [C.POINTER(lbm_physical), C.POINTER(lbm_params), _dp,
+                                           C.POINTER(C.c_char_p)]),
     "lbm_get_omega": (C.c_int, [C.c_void_p, _dp]),
     "lbm_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, _dp]),
     "lbm_init_fields": (C.c_int, [C.c_void_p, _dp, _dp, C.c_int32]),
@@ -136,6 +145,8 @@ _SIGS = {
     "lbm_server_result": (C.c_int, [C.c_void_p, C.c_int64, _dp, _dp]),
     "lbm_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_server_info": (C.c_int, [C.c_void_p, _dp]),
+    "lbm_server_check_request": (C.c_int, [C.POINTER(lbm_request), C.c_int64, C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_char_p)]),
 }
 
 
@@ -188,24 +199,35 @@ def params_check(p):
     return nu.value, omega.value
 
 
+def params_from_physical(Re, delta_r, rho, mu, d_thr, delta_t=0.0, CFL=0.0, **kw):
+    """lbm_params_from_physical: (lbm_params, dict) of a run given in
+    physical units (SI).  The params hold Re, u_char and L_char (plus any
+    make_params keywords); the dict holds Re, L_char, u_char, nu, CFL and
+    delta_t.  Give delta_t, or CFL for the time step of the CFL rule."""
+    ph = lbm_physical(Re=float(Re), d_thr=float(d_thr), rho=float(rho), mu=float(mu), delta_r=float(delta_r),
+                      delta_t=float(delta_t), CFL=float(CFL))
+    p = make_params(**kw)
+    out = (C.c_double * 5)()
+    why = C.c_char_p()
+    st = capi().lbm_params_from_physical(C.byref(ph), C.byref(p), out, C.byref(why))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_params_from_physical: " + why.value.decode())
+    lu = dict(zip(["L_char", "u_char", "nu", "CFL", "delta_t"], list(out)))
+    lu["Re"] = float(Re)
+    return p, lu
+
+
 def lattice_units(Re, delta_r, delta_t, rho, mu, d_thr):
-    """Lattice parameters of a run given in physical units (SI) (Sec. 2.2).
-    The Reynolds number on the throat fixes the throat mean velocity
-    u_thr = mu Re / (rho d_thr); in cells and steps the characteristic length
-    is L_char = d_thr / delta_r, the velocity u_char = u_thr delta_t / delta_r
-    (half the CFL number of Sec. 2.2) and the viscosity
-    nu = mu delta_t / (rho delta_r^2).  Returns a dict with Re, L_char,
-    u_char, nu and CFL; Re, u_char and L_char feed make_params."""
-    u_thr = mu * Re / (rho * d_thr)
-    u_char = u_thr * delta_t / delta_r
-    return dict(Re=Re, L_char=d_thr / delta_r, u_char=u_char, nu=mu * delta_t / (rho * delta_r ** 2),
-                CFL=2.0 * u_char)
+    """Lattice units of a physical run with a given time step
+    (lbm_params_from_physical): dict with Re, L_char, u_char, nu, CFL and
+    delta_t."""
+    return params_from_physical(Re, delta_r, rho, mu, d_thr, delta_t=delta_t)[1]
 
 
 def cfl_time_step(Re, delta_r, CFL, rho, mu, d_thr):
-    """Time step (s) that puts the throat mean velocity at the given CFL
-    number, CFL = 2 u_thr delta_t / delta_r (Sec. 2.2 time-step rule)."""
-    return rho * d_thr * delta_r * CFL / (2.0 * mu * Re)
+    """Time step (s) of the CFL rule for a physical run
+    (lbm_params_from_physical with a CFL number instead of a time step)."""
+    return params_from_physical(Re, delta_r, rho, mu, d_thr, CFL=CFL)[1]["delta_t"]
 
 
 def make_nozzle(D, d, L_total, L_in=None, L_cone=-1, L_throat=None, half_angle_deg=10.0):
@@ -268,7 +290,7 @@ class Lattice:
     """
 
     def __init__(self, flags, precision="fp32", periodic=0, fp16_scale=0.0, device=0, stream=None,
-                 torch_allocator=True):
+                 torch_allocator=True, allocator=None):
         import torch
 
         self.lib = capi()
@@ -280,7 +302,10 @@ class Lattice:
         nz, ny, nx = flags.shape
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
-        self.allocator = TorchAllocator(device, self.stream) if torch_allocator else None
+        if allocator is not None:  # any object with struct() -> lbm_allocator
+            self.allocator = allocator
+        else:
+            self.allocator = TorchAllocator(device, self.stream) if torch_allocator else None
         d = lbm_desc()
         d.nx, d.ny, d.nz = nx, ny, nz
         d.periodic = int(periodic)
@@ -297,7 +322,11 @@ class Lattice:
             raise LbmError(st, "lbm_create")
         self.ctx = ctx
         self.precision = precision
-        self._check(self.lib.lbm_set_geometry(self.ctx, flags.ctypes.data))
+        try:
+            self._check(self.lib.lbm_set_geometry(self.ctx, flags.ctypes.data))
+        except LbmError:
+            self.close()
+            raise
         n = C.c_int64()
         self._check(self.lib.lbm_fluid_count(self.ctx, C.byref(n)))
         self.n_active = n.value
@@ -467,17 +496,49 @@ class Lattice:
         return dict(slots=s.value, buffer_bytes=b.value, device_bytes=d.value)
 
 
+def make_request(flags, steps, precision="fp32", periodic=0, fp16_scale=0.0, **params):
+    """An lbm_request over a C-contiguous uint8 flag array (nz, ny, nx), which
+    the caller keeps alive while the request is in use."""
+    nz, ny, nx = flags.shape
+    r = lbm_request()
+    r.nx, r.ny, r.nz, r.periodic = nx, ny, nz, int(periodic)
+    r.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    r.fp16_scale = float(fp16_scale)
+    r.flags = flags.ctypes.data
+    r.params = make_params(**params)
+    r.steps = int(steps)
+    return r
+
+
+def check_request(flags, steps, precision="fp32", budget_bytes=1 << 40, periodic=0, fp16_scale=0.0, **params):
+    """lbm_server_check_request (host only): the checks a request server
+    applies to a request, with its index build.  Returns a dict of counts;
+    raises LbmError with the reason of a refusal."""
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    r = make_request(flags, steps, precision, periodic, fp16_scale, **params)
+    out = (C.c_int64 * 4)()
+    why = C.c_char_p()
+    st = capi().lbm_server_check_request(C.byref(r), int(budget_bytes), out, C.byref(why))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_server_check_request: " + why.value.decode())
+    return dict(zip(["active", "slots", "footprint", "boundary_nodes"], list(out)))
+
+
 class Server:
     """A request server (lbm_server_create .. lbm_server_destroy): continuous
     batching of many lattices on one GPU.  Memory comes from PyTorch's
     caching allocator; work runs on a dedicated torch stream."""
 
-    def __init__(self, budget_bytes, max_slots=32, steps_per_tick=32, device=0, stream=None, torch_allocator=True):
+    def __init__(self, budget_bytes, max_slots=32, steps_per_tick=32, device=0, stream=None, torch_allocator=True,
+                 allocator=None):
         import torch
 
         self.lib = capi()
         self.stream = stream if stream is not None else torch.cuda.Stream(device)
-        self.allocator = TorchAllocator(device, self.stream) if torch_allocator else None
+        if allocator is not None:  # any object with struct() -> lbm_allocator
+            self.allocator = allocator
+        else:
+            self.allocator = TorchAllocator(device, self.stream) if torch_allocator else None
         d = lbm_server_desc()
         d.device = device
         d.stream = C.c_void_p(self.stream.cuda_stream)
@@ -500,14 +561,7 @@ class Server:
 
     def submit(self, flags, steps, precision="fp32", periodic=0, fp16_scale=0.0, **params):
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
-        nz, ny, nx = flags.shape
-        r = lbm_request()
-        r.nx, r.ny, r.nz, r.periodic = nx, ny, nz, int(periodic)
-        r.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        r.fp16_scale = float(fp16_scale)
-        r.flags = flags.ctypes.data
-        r.params = make_params(**params)
-        r.steps = int(steps)
+        r = make_request(flags, steps, precision, periodic, fp16_scale, **params)
         rid = C.c_int64()
         self._check(self.lib.lbm_server_submit(self.h, C.byref(r), C.byref(rid)))
         return rid.value

@@ -61,8 +61,12 @@ def run_stream(specs, budget_bytes, max_slots=32, steps_per_tick=32, precision=N
                 state, _ = srv.poll(rid)
                 if state in (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED, lbm.LBM_REQ_CANCELLED):
                     cells = srv.cells(rid)
-                    res = srv.result(rid) if state == lbm.LBM_REQ_DONE else None
-                    done[k] = dict(state=state, finish=now, cells=cells, result=res)
+                    res, err = None, None
+                    try:  # releases the request whatever its outcome
+                        res = srv.result(rid)
+                    except lbm.LbmError as e:
+                        err = e
+                    done[k] = dict(state=state, finish=now, cells=cells, result=res, error=err)
             if running == 0 and queued == 0 and nxt < len(order):
                 time.sleep(max(0.0, specs[order[nxt]]["arrival"] * time_scale - (time.perf_counter() - t0)))
         info = srv.info()

@@ -77,10 +77,13 @@ def test_table2_time_steps_follow_the_cfl_rule(lbm):
 
 def test_table2_lattice_parameters_give_the_relaxation_time(lbm):
     for lv, Re, dr, dt in table2():
-        lu = lbm.lattice_units(Re, dr, dt, RHO, MU, D_THR)
-        assert abs(lu["CFL"] - cfl_of(Re, dr, dt)) < 1e-12
-        # the library's route: nu = u_char L_char / Re, omega = 1 / (3 nu + 1/2)
-        p = lbm.make_params(Re=lu["Re"], u_char=lu["u_char"], L_char=lu["L_char"])
+        # the library's route (lbm_params_from_physical, then lbm_params_check):
+        # u_char, L_char from the physical run, nu = u_char L_char / Re,
+        # omega = 1 / (3 nu + 1/2)
+        p, lu = lbm.params_from_physical(Re, dr, RHO, MU, D_THR, delta_t=dt)
+        assert abs(lu["CFL"] / cfl_of(Re, dr, dt) - 1.0) < 1e-12
+        assert lu["delta_t"] == dt and abs(lu["L_char"] - D_THR / dr) < 1e-12 * lu["L_char"]
+        assert (p.Re, p.u_char, p.L_char, p.nu) == (Re, lu["u_char"], lu["L_char"], 0.0)
         nu, omega = lbm.params_check(p)
         # the paper's route in physical units (Sec. 2.1): tau = mu / (rho theta0) + dt / 2
         # with theta0 = dr^2 / (3 dt^2); omega = dt / tau
@@ -90,6 +93,22 @@ def test_table2_lattice_parameters_give_the_relaxation_time(lbm):
         assert abs(nu / lu["nu"] - 1.0) < 1e-12
         # under-resolved regime of the paper: tau close to 1/2
         assert 0.5 < 1.0 / omega < 0.52
+
+
+def test_params_from_physical_checks(lbm):
+    # the CFL route and the time-step route agree
+    dt = lbm.cfl_time_step(3500.0, 1.725e-4, 0.249, RHO, MU, D_THR)
+    _, lu = lbm.params_from_physical(3500.0, 1.725e-4, RHO, MU, D_THR, delta_t=dt)
+    assert abs(lu["CFL"] / 0.249 - 1.0) < 1e-14
+    # other fields of the params are kept
+    p, _ = lbm.params_from_physical(500.0, 2.3e-4, RHO, MU, D_THR, CFL=0.17, u_in=0.01, noise_amp=0.02)
+    assert p.u_in == 0.01 and p.noise_amp == 0.02 and p.Re == 500.0
+    for kw, word in [(dict(CFL=0.0), "CFL"), (dict(CFL=2.5), "sound speed"), (dict(CFL=0.2, mu=0.0), "> 0")]:
+        args = dict(Re=3500.0, delta_r=1e-4, rho=RHO, mu=MU, d_thr=D_THR)
+        args.update(kw)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.params_from_physical(**args)
+        assert e.value.status == lbm.LBM_ERR_ARG and word in str(e.value), kw
 
 
 def test_ladder_levels_follow_table2():

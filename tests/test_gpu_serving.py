@@ -125,10 +125,12 @@ def test_cancel_queued_and_running(mods):
         srv.close()
 
 
-def test_diverging_lattice_does_not_disturb_the_others(mods):
+def test_diverging_lattice_is_evicted_and_does_not_disturb_the_others(mods):
     """A lattice driven far beyond the low-Mach regime (host-side fault
-    injection through its parameters) runs beside others; theirs results are
-    unchanged, bit for bit."""
+    injection through its parameters) runs beside others.  The health check
+    at the end of a tick finds its non-finite state: it is evicted and ends
+    FAILED with LBM_ERR_UNSTABLE, its memory is freed, and the others'
+    results are unchanged, bit for bit."""
     lbm, serving = mods
     base = [dict(MIX[0]), dict(MIX[1])]
     ref = serving.run_stream([dict(s) for s in base], budget_bytes=4 << 30, steps_per_tick=16)
@@ -136,12 +138,66 @@ def test_diverging_lattice_does_not_disturb_the_others(mods):
     try:
         ids = [srv.submit(serving.request_geometry(s), s["steps"], s["precision"], **serving.request_params(s))
                for s in base]
-        bad = srv.submit(I.pipe_flags(12, 40), 120, "fp32", nu=1e-7, u_in=0.55, profile="plug")
-        tick_until(srv, lambda: all(srv.poll(i)[0] == lbm.LBM_REQ_DONE for i in ids + [bad]))
+        bad = srv.submit(I.pipe_flags(12, 40), 4000, "fp32", nu=1e-7, u_in=0.55, profile="plug")
+        terminal = (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED)
+        tick_until(srv, lambda: all(srv.poll(i)[0] in terminal for i in ids + [bad]))
         for k, i in enumerate(ids):
+            assert srv.poll(i)[0] == lbm.LBM_REQ_DONE
             r, u = srv.result(i)
             rr, ur = ref["results"][k]["result"]
             assert np.array_equal(r, rr) and np.array_equal(u, ur)
-        assert srv.poll(bad)[0] == lbm.LBM_REQ_DONE
+        state, steps_done = srv.poll(bad)
+        assert state == lbm.LBM_REQ_FAILED and 0 < steps_done < 4000
+        with pytest.raises(lbm.LbmError) as e:
+            srv.result(bad)
+        assert e.value.status == lbm.LBM_ERR_UNSTABLE and "non-finite" in str(e.value)
+        with pytest.raises(lbm.LbmError):  # released: the id is no longer known
+            srv.poll(bad)
+        tick_until(srv, lambda: srv.tick() == (0, 0))
+        assert srv.info()["bytes_in_use"] == 0
+    finally:
+        srv.close()
+
+
+def test_oversized_lattice_fails_without_running(mods):
+    """A request whose index needs more slots than the server's 32-bit
+    population offsets address passes submit's cheap checks (few active
+    cells) and ends FAILED once its index is built; nothing is allocated for
+    it and no kernel touches it.  Other requests are served normally."""
+    lbm, serving = mods
+    nx = (1 << 20) - 1
+    f = np.zeros((11, 11, nx), dtype=np.uint8)
+    f[:, :, 0] = 1
+    f[:, :, -1] = 1
+    srv = lbm.Server(budget_bytes=4 << 30, max_slots=4, steps_per_tick=8)
+    try:
+        big = srv.submit(f, 10, "fp32", nu=0.01)
+        ok = srv.submit(I.pipe_flags(6, 12), 16, "fp32", nu=0.01, u_in=0.01)
+        terminal = (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED)
+        tick_until(srv, lambda: all(srv.poll(i)[0] in terminal for i in (big, ok)))
+        assert srv.poll(big) == (lbm.LBM_REQ_FAILED, 0)
+        with pytest.raises(lbm.LbmError) as e:
+            srv.result(big)
+        assert e.value.status == lbm.LBM_ERR_ARG and "storage slots" in str(e.value)
+        assert srv.poll(ok)[0] == lbm.LBM_REQ_DONE
+        assert srv.info()["peak_bytes"] < 1 << 24
+    finally:
+        srv.close()
+
+
+def test_cancelled_requests_are_released(mods):
+    lbm, serving = mods
+    srv = lbm.Server(budget_bytes=1 << 30, max_slots=2, steps_per_tick=4)
+    try:
+        g = I.pipe_flags(8, 20)
+        a = srv.submit(g, 100, "fp32", nu=0.02, u_in=0.01)
+        srv.cancel(a)
+        tick_until(srv, lambda: srv.poll(a)[0] == lbm.LBM_REQ_CANCELLED)
+        with pytest.raises(lbm.LbmError) as e:
+            srv.result(a)
+        assert e.value.status == lbm.LBM_ERR_STATE and "cancelled" in str(e.value)
+        with pytest.raises(lbm.LbmError) as e:
+            srv.poll(a)
+        assert e.value.status == lbm.LBM_ERR_ARG
     finally:
         srv.close()
