@@ -1,12 +1,18 @@
 """Benchmark of the fused D3Q27 central-Hermite MRT stream-collide step on GB300.
 
-One "step" is one lattice time step over the whole workload (one fused
-kernel launch: pull gather, collision, bounce-back, inlet/outlet).  Default
-workload: the Re 3500 transitional nozzle on a 96 x 96 x 800 lattice
-(4 286 996 active cells), FP32 populations; FP16-shifted and FP64 storage are
-timed on the same workload for the precision comparison.  Inputs are seeded
-and synthetic; the population buffers (>= 0.28 GB each) exceed the 129 MB L2,
-so no flush is needed between steps.
+One "step" is one lattice time step over the whole workload (the fused
+fluid kernel: pull gather, collision, bounce-back; and the inlet/outlet
+nodes).  Default workload: the Re 6500 turbulent nozzle on a 144 x 144 x 1200
+lattice (14 471 488 active cells), the largest of the nozzle workloads,
+FP32 populations; FP16-shifted and FP64 storage are timed on the same
+workload for the precision comparison.  Inputs are seeded and synthetic; the
+population buffers (>= 0.9 GB each) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+Timing: after W warm-up steps, regions of exactly K steps are timed with
+CUDA events on the library's stream, each bracketed by a barrier and a
+device synchronisation, repeated until at least --min-seconds of timed work
+(and at least 5 regions); the median region gives ms_per_step.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle instead (a bounded sample of the same workload per step).
@@ -26,7 +32,7 @@ if ROOT not in sys.path:
 
 METRIC = "fluid MLUPS & % HBM roofline (FP32/FP16 vs FP64); serving p50/p99 latency"
 UNIT = "fluid MLUPS"
-DEFAULT_WORKLOAD = "nozzle_re3500_96x96x800"
+DEFAULT_WORKLOAD = "nozzle_re6500_144x144x1200"
 STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16 storage / f32 arithmetic"}
 LINK_WORD_BYTES = 4
@@ -48,19 +54,22 @@ def algorithmic_bytes_per_cell(precision):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precisions", default="fp32,fp16s,fp64",
                     help="first one is the headline; others are reported under by_precision")
-    ap.add_argument("--fp64-steps", type=int, default=1000)
+    ap.add_argument("--min-seconds", type=float, default=3.0,
+                    help="timed work per precision: K-step regions are repeated until this much (at least 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-seconds", type=float, default=150.0,
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="oracle time of the whole --impl reference run (warm-up and timed steps)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
+    ap.add_argument("--serving-stream", choices=["scaled", "full"], default="scaled",
+                    help="full: the request mix at its full sizes (d 8-48, 2000-20000 steps; minutes)")
     return ap.parse_args()
 
 
@@ -198,7 +207,42 @@ def aggregate_replicas(ms_local, cells_local, steps, dist=None, device="cpu"):
 
 # --------------------------------------------------------------- our kernels
 
-def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup, dist=None, sampler=None):
+def timed_regions(torch, stream, run_region, steps, min_seconds, dist=None, device="cpu", min_repeats=5,
+                  max_repeats=5000):
+    """Time regions of exactly `steps` steps (run_region enqueues one) with
+    CUDA events on `stream`, each bracketed by a barrier and a device
+    synchronisation; the count of regions fills about min_seconds (at least
+    min_repeats), agreed over ranks.  Returns the per-region milliseconds."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)  # probe region (not reported): sizes the repeat count
+    run_region()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    probe_s = max(e0.elapsed_time(e1) * 1e-3, 1e-6)
+    reps = int(min(max_repeats, max(min_repeats, -(-min_seconds // probe_s))))
+    if dist is not None:
+        t = torch.tensor([float(reps)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        reps = int(t.item())
+    times = []
+    for _ in range(reps):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run_region()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup, min_seconds, dist=None,
+                   sampler=None, device="cpu"):
+    """Median milliseconds of a K-step region of one precision (max over
+    ranks is taken by the caller)."""
     from paper_2204_10566_gb300 import inputs as I
 
     G = lbm.Lattice(flags, precision, periodic=periodic)
@@ -206,26 +250,16 @@ def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup
     n = G.n_active
     G.init_fields(I.random_density_field(n, 0.001, 3), I.random_velocity_field(n, 0.01, 4))
     G.step(warmup).sync()
-    stream = G.stream
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
     if sampler:
         sampler.start()
-    e0.record(stream)
-    G.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    times = timed_regions(torch, G.stream, lambda: G.step(steps), steps, min_seconds, dist, device)
     clocks = sampler.stop() if sampler else None
-    if dist is not None:
-        dist.barrier()
     G.sync()
-    ms = e0.elapsed_time(e1)
     info = G.layout_info()
     G.close()
-    return n, ms, clocks, info
+    timing = {"regions": len(times), "steps_per_region": steps, "stat": "median",
+              "ms_region_min": min(times), "ms_region_max": max(times)}
+    return n, statistics.median(times), clocks, info, timing
 
 
 def e2e_run(lbm, torch, flags, params, periodic, precision, steps):
@@ -262,7 +296,12 @@ def e2e_run(lbm, torch, flags, params, periodic, precision, steps):
 class OracleSample:
     """The FP64 CPU oracle on a sub-box of the workload (a z-slab from the
     middle of the lattice, cut in y when one plane is already too much),
-    sized from a one-plane calibration to about target_seconds per step."""
+    sized from a one-plane calibration to about target_seconds per step.
+    The sample lattice is built and initialised once (uniform equilibrium,
+    rho = 1, u = (0, 0, 0.01)); each timed sample continues from the state
+    the previous one left."""
+
+    U0 = (0.0, 0.0, 0.01)
 
     def __init__(self, flags, params, periodic, target_seconds):
         import numpy as np
@@ -270,13 +309,14 @@ class OracleSample:
         import oracle
 
         self.oracle = oracle
+        self.np = np
         nz, ny, nx = flags.shape
         nu = params.get("nu") or params["u_char"] * params["L_char"] / params["Re"]
         self.omega = 1.0 / (3.0 * nu + 0.5)
         self.periodic = periodic & 3
         z0 = nz // 2
         plane = np.array(flags[z0:z0 + 1])
-        dt, cells = self._run(plane)
+        dt, cells = self._time(self._lattice(plane), 1)
         per_cell = dt / max(cells, 1)
         want = max(1, int(target_seconds / per_cell))
         if want >= cells:
@@ -285,83 +325,94 @@ class OracleSample:
             planes, rows = 1, max(2, int(ny * want / max(cells, 1)))
         self.flags = np.array(flags[z0:z0 + planes, :rows, :])
         self.cells = int((self.flags != 0).sum())
+        self.L = self._lattice(self.flags)
         # a slab capped at the far end of the lattice takes several steps,
         # counted from one timed step of the slab itself
         self.steps = 1
         if planes == nz - z0 and rows == ny:
-            dt1, _ = self._run(self.flags)
+            dt1, _ = self._time(self.L, 1)
             self.steps = max(1, int(round(target_seconds / max(dt1, 1e-9))))
         self.threads = os.cpu_count() or 1
         self.desc = "%d oracle step%s on a %dx%dx%d sub-box (z from %d) of the workload, %d active cells" % (
             self.steps, "s" if self.steps > 1 else "", nx, rows, planes, z0, self.cells)
 
-    def _run(self, f, steps=1):
-        L = self.oracle.Lattice(f, self.omega, periodic=self.periodic)
-        L.init_equilibrium(1.0, [0.0, 0.0, 0.01])
+    def _lattice(self, f, nthreads=0):
+        """An oracle lattice of flags f at the uniform equilibrium (the same
+        populations init_equilibrium gives every active cell)."""
+        np = self.np
+        L = self.oracle.Lattice(f, self.omega, periodic=self.periodic, nthreads=nthreads)
+        pop = np.zeros((f.size, 27))
+        pop[f.reshape(-1) != 0] = self.oracle.equilibrium(1.0, np.array(self.U0))
+        L.set_populations(pop)
+        return L
+
+    @staticmethod
+    def _time(L, steps):
         t = time.perf_counter()
         L.step(steps)
-        return time.perf_counter() - t, int((f != 0).sum()) * steps
+        return time.perf_counter() - t, int((L.flags != 0).sum()) * steps
 
     def single_thread(self):
         """One oracle step on the first 16 z-planes of the slab with one
         thread: returns (MLUPS, cells)."""
-        import numpy as np
-
-        plane = np.array(self.flags[:16])
-        L = self.oracle.Lattice(plane, self.omega, periodic=self.periodic, nthreads=1)
-        L.init_equilibrium(1.0, [0.0, 0.0, 0.01])
-        t = time.perf_counter()
-        L.step(1)
-        dt = time.perf_counter() - t
-        cells = int((plane != 0).sum())
+        plane = self.np.array(self.flags[:16])
+        dt, cells = self._time(self._lattice(plane, nthreads=1), 1)
         return cells / dt / 1e6, cells
 
     def step(self):
         """One timed sample; returns (MLUPS, seconds)."""
-        dt, updates = self._run(self.flags, self.steps)
+        dt, updates = self._time(self.L, self.steps)
         return updates / dt / 1e6, dt
 
 
 # ----------------------------------------------------------------- serving
 
-SERVING_D = (8, 24)
-SERVING_STEPS = (200, 2000)
+SERVING_STREAMS = {
+    # scaled down from the full mix so that the default measurement takes seconds
+    "scaled": dict(d=(8, 24), steps=(200, 2000)),
+    # the request mix at its full sizes
+    "full": dict(d=(8, 48), steps=(2000, 20000)),
+}
 
 
-def serving_measurement(capacity_mlups, n_requests):
+def serving_measurement(capacity_mlups, n_requests, stream="scaled"):
     """Continuous batching on the seeded request stream (nozzle / pipe runs of
     throat diameter d, D = 3 d, L = 25 d, Re uniform in 500-6500, FP32 or
     FP16S with p = 1/2, Poisson arrivals at 1.2 x the measured single-stream
     FP32 capacity), against the same stream run back to back as plain FP32
     lattices, and again at 0.5 x the capacity (latency of an unsaturated
-    server).  Sizes and step counts are scaled down from the full request mix
-    (d 8-48, 2000-20000 steps) so that the measurement takes seconds."""
+    server).  stream "full" is the request mix at its sizes (d 8-48,
+    2000-20000 steps); "scaled" shrinks both so that it takes seconds."""
     import torch
 
     from paper_2204_10566_gb300 import inputs as I
-    from paper_2204_10566_gb300 import lbm, serving
+    from paper_2204_10566_gb300 import serving
 
-    probe = I.serving_requests(n=n_requests, seed=2204, rate=1.0, d_range=SERVING_D, steps_range=SERVING_STEPS)
+    d_range, steps_range = SERVING_STREAMS[stream]["d"], SERVING_STREAMS[stream]["steps"]
+    probe = I.serving_requests(n=n_requests, seed=2204, rate=1.0, d_range=d_range, steps_range=steps_range)
     work = []
     for s in probe:
         f = serving.request_geometry(s)
         work.append(I.active_count(f) * s["steps"])
     rate = 1.2 * capacity_mlups * 1e6 / (sum(work) / len(work))
-    specs = I.serving_requests(n=n_requests, seed=2204, rate=rate, d_range=SERVING_D, steps_range=SERVING_STEPS)
+    specs = I.serving_requests(n=n_requests, seed=2204, rate=rate, d_range=d_range, steps_range=steps_range)
     free, _ = torch.cuda.mem_get_info()
     srv = serving.run_stream([dict(s) for s in specs], budget_bytes=int(0.5 * free), max_slots=32, steps_per_tick=32)
     b2b = serving.run_back_to_back([dict(s) for s in specs], "fp32")
     # the same stream at 0.5x the capacity: latency when the server is not saturated
-    low = I.serving_requests(n=n_requests, seed=2204, rate=rate * 0.5 / 1.2, d_range=SERVING_D,
-                             steps_range=SERVING_STEPS)
+    low = I.serving_requests(n=n_requests, seed=2204, rate=rate * 0.5 / 1.2, d_range=d_range,
+                             steps_range=steps_range)
     srv_low = serving.run_stream([dict(s) for s in low], budget_bytes=int(0.5 * free), max_slots=32,
                                  steps_per_tick=32)
+    failed = [dict(d=specs[k]["d"], Re=round(specs[k]["Re"]), steps=specs[k]["steps"], kind=specs[k]["kind"],
+                   precision=specs[k]["precision"], steps_done=r["steps_done"], error=str(r["error"]))
+              for k, r in srv["results"].items() if r["state"] != 2]
     return {
         "low_load": {"offered_load": 0.5, "p50_s": srv_low["latency_p50_s"], "p99_s": srv_low["latency_p99_s"],
                      "aggregate_mlups": srv_low["mlups"]},
-        "requests": n_requests, "arrival_rate_per_s": rate, "offered_load": 1.2,
-        "stream": "seed 2204; d uniform in %d-%d (D = 3d, L = 25d), Re 500-6500, %d-%d steps, FP32/FP16S, "
-                  "nozzle/pipe; scaled from d 8-48 and 2000-20000 steps" % (SERVING_D + SERVING_STEPS),
+        "requests": n_requests, "arrival_rate_per_s": rate, "offered_load": 1.2, "failed_requests": failed,
+        "stream": "%s: seed 2204; d uniform in %d-%d (D = 3d, L = 25d), Re 500-6500, %d-%d steps, FP32/FP16S, "
+                  "nozzle/pipe" % ((stream,) + tuple(d_range) + tuple(steps_range)),
         "p50_s": srv["latency_p50_s"], "p99_s": srv["latency_p99_s"],
         "aggregate_mlups": srv["mlups"], "makespan_s": srv["makespan_s"],
         "back_to_back_fp32_mlups": b2b["mlups"], "back_to_back_s": b2b["seconds"],
@@ -426,8 +477,8 @@ def ours_arm(args):
     peak, peak_kind = load_peaks()
 
     sampler = ClockSampler(device) if rank == 0 else None
-    n, ms, clocks, info = time_precision(lbm, torch, flags, params, periodic, head, args.steps, args.warmup, dist,
-                                         sampler)
+    n, ms, clocks, info, timing = time_precision(lbm, torch, flags, params, periodic, head, args.steps, args.warmup,
+                                                 args.min_seconds, dist, sampler, device="cuda")
     ms_max, _, value = aggregate_replicas(ms, n, args.steps, dist, device="cuda")
     per_launch_s = ms * 1e-3 / max(args.steps, 1)
     alg_bytes = algorithmic_bytes_per_cell(head) * n
@@ -436,9 +487,10 @@ def ours_arm(args):
 
     by_prec = {}
     for p in precisions[1:]:
-        steps = args.fp64_steps if p == "fp64" else args.steps
-        n_p, ms_p, _, info_p = time_precision(lbm, torch, flags, params, periodic, p, steps,
-                                              min(args.warmup, 20), dist, None)
+        steps = args.steps
+        n_p, ms_p, _, info_p, timing_p = time_precision(lbm, torch, flags, params, periodic, p, steps, args.warmup,
+                                                        0.5 * args.min_seconds, dist, None, device="cuda")
+        ms_p = aggregate_replicas(ms_p, n_p, steps, dist, device="cuda")[0]
         ach_p = algorithmic_bytes_per_cell(p) * n_p / (ms_p * 1e-3 / steps) / 1e9
         if p == "fp64":
             tf = FP64_FLOPS_PER_CELL * n_p / (ms_p * 1e-3 / steps) / 1e12
@@ -448,8 +500,10 @@ def ours_arm(args):
         else:
             roof = {"bound": "hbm", "achieved": ach_p, "peak": peak, "unit": "GB/s", "frac": ach_p / peak,
                     "peak_kind": peak_kind, "bytes_per_cell": algorithmic_bytes_per_cell(p)}
+        if p != "fp64":
+            roof["traffic"] = recorded_traffic(args.workload, p)
         by_prec[p] = {"value": world * n_p * steps / (ms_p * 1e-3) / 1e6, "unit": UNIT, "steps": steps,
-                      "ms_per_step": ms_p / steps, "roofline": roof}
+                      "ms_per_step": ms_p / steps, "roofline": roof, "timing": timing_p}
 
     if rank != 0:
         if dist is not None:
@@ -458,7 +512,7 @@ def ours_arm(args):
     e2e = e2e_run(lbm, torch, flags, params, periodic, head, args.steps)
     serve = None
     if world == 1 and not args.no_serving:
-        serve = serving_measurement(value, args.serving_requests)
+        serve = serving_measurement(value, args.serving_requests, args.serving_stream)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         sample = OracleSample(flags, params, periodic, args.cpu_seconds)
@@ -483,6 +537,7 @@ def ours_arm(args):
         "by_precision": by_prec,
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step(flags, periodic, head),
+        "timing": dict(timing, note="gpu_launches counts the kernels of one timed K-step region"),
         "clocks": clocks,
         "cpu_baseline": cpu,
         "serving": serve,

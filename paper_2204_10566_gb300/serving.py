@@ -58,7 +58,7 @@ def run_stream(specs, budget_bytes, max_slots=32, steps_per_tick=32, precision=N
             for k, rid in ids.items():
                 if k in done:
                     continue
-                state, _ = srv.poll(rid)
+                state, steps_done = srv.poll(rid)
                 if state in (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED, lbm.LBM_REQ_CANCELLED):
                     cells = srv.cells(rid)
                     res, err = None, None
@@ -66,14 +66,16 @@ def run_stream(specs, budget_bytes, max_slots=32, steps_per_tick=32, precision=N
                         res = srv.result(rid)
                     except lbm.LbmError as e:
                         err = e
-                    done[k] = dict(state=state, finish=now, cells=cells, result=res, error=err)
+                    done[k] = dict(state=state, finish=now, cells=cells, steps_done=steps_done, result=res,
+                                   error=err)
             if running == 0 and queued == 0 and nxt < len(order):
                 time.sleep(max(0.0, specs[order[nxt]]["arrival"] * time_scale - (time.perf_counter() - t0)))
         info = srv.info()
     finally:
         srv.close()
     lat = np.array([done[k]["finish"] - specs[k]["arrival"] * time_scale for k in range(len(specs))])
-    updates = sum(done[k]["cells"] * specs[k]["steps"] for k in range(len(specs)))
+    # cell updates the server actually ran (a failed request stops early)
+    updates = sum(done[k]["cells"] * done[k]["steps_done"] for k in range(len(specs)))
     makespan = max(done[k]["finish"] for k in done) - min(s["arrival"] * time_scale for s in specs)
     return dict(results=done, latency_p50_s=float(np.percentile(lat, 50)), latency_p99_s=float(np.percentile(lat, 99)),
                 cell_updates=float(updates), makespan_s=float(makespan), mlups=updates / makespan / 1e6, info=info)

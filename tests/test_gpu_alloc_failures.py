@@ -91,12 +91,17 @@ def test_failures_after_set_up_keep_the_context_usable(lbm):
         with pytest.raises(lbm.LbmError) as e:
             G.init_fields(np.ones(G.n_active), np.zeros((G.n_active, 3)))
         assert e.value.status == lbm.LBM_ERR_OOM and a.live == held
-        # the context still works
+        # the context still works: the same state as a run that saw no failure
         a.fail_at = set()
         G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
         G.step(4).sync()
         rho, u = G.moments()
-        assert np.isfinite(u).all() and abs(rho.mean() - 1.0) < 1e-3
+        with lbm.Lattice(FLAGS, "fp32") as R:
+            R.set_params(nu=0.02, u_in=0.01)
+            R.init_equilibrium(1.0, (0.0, 0.0, 0.0))
+            R.step(4).sync()
+            rho_r, u_r = R.moments()
+        assert np.array_equal(rho, rho_r) and np.array_equal(u, u_r) and np.abs(u).max() > 0
         G.stats_begin(1)
         G.step(2).sync()
         assert G.stats_get()[2] == 2
