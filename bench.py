@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="oracle time of the whole --impl reference run (warm-up and timed steps)")
+    ap.add_argument("--row-axis", choices=["auto", "x", "z"], default="auto",
+                    help="axis of the storage rows (auto: z for the nozzles, the flow axis)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-stream", choices=["scaled", "full"], default="scaled",
@@ -240,12 +242,12 @@ def timed_regions(torch, stream, run_region, steps, min_seconds, dist=None, devi
 
 
 def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup, min_seconds, dist=None,
-                   sampler=None, device="cpu"):
+                   sampler=None, device="cpu", row_axis="auto"):
     """Median milliseconds of a K-step region of one precision (max over
     ranks is taken by the caller)."""
     from paper_2204_10566_gb300 import inputs as I
 
-    G = lbm.Lattice(flags, precision, periodic=periodic)
+    G = lbm.Lattice(flags, precision, periodic=periodic, row_axis=row_axis)
     G.set_params(**params)
     n = G.n_active
     G.init_fields(I.random_density_field(n, 0.001, 3), I.random_velocity_field(n, 0.01, 4))
@@ -478,7 +480,8 @@ def ours_arm(args):
 
     sampler = ClockSampler(device) if rank == 0 else None
     n, ms, clocks, info, timing = time_precision(lbm, torch, flags, params, periodic, head, args.steps, args.warmup,
-                                                 args.min_seconds, dist, sampler, device="cuda")
+                                                 args.min_seconds, dist, sampler, device="cuda",
+                                                 row_axis=args.row_axis)
     ms_max, _, value = aggregate_replicas(ms, n, args.steps, dist, device="cuda")
     per_launch_s = ms * 1e-3 / max(args.steps, 1)
     alg_bytes = algorithmic_bytes_per_cell(head) * n
@@ -489,7 +492,8 @@ def ours_arm(args):
     for p in precisions[1:]:
         steps = args.steps
         n_p, ms_p, _, info_p, timing_p = time_precision(lbm, torch, flags, params, periodic, p, steps, args.warmup,
-                                                        0.5 * args.min_seconds, dist, None, device="cuda")
+                                                        0.5 * args.min_seconds, dist, None, device="cuda",
+                                                        row_axis=args.row_axis)
         ms_p = aggregate_replicas(ms_p, n_p, steps, dist, device="cuda")[0]
         ach_p = algorithmic_bytes_per_cell(p) * n_p / (ms_p * 1e-3 / steps) / 1e9
         if p == "fp64":
@@ -527,6 +531,7 @@ def ours_arm(args):
         "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
         "config": {"workload": args.workload, "precision": head, "active_cells": n, "box": list(flags.shape[::-1]),
                    "slots": info["slots"], "Re": w.get("Re"),
+                   "row_axis": lbm.check_layout(flags, periodic, args.row_axis)["row_axis"],
                    "l2": "inputs larger than L2 (population buffers %.2f GB each)" % (info["buffer_bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -65,6 +65,11 @@ enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
 enum { LBM_PROFILE_PLUG = 0, LBM_PROFILE_PARABOLIC = 1 };
 enum { LBM_LAYOUT_ACTIVE = 0, LBM_LAYOUT_BOX = 1 };
 enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
+/* Axis along which the populations are stored in contiguous rows (a storage
+ * choice: results do not depend on it beyond floating-point contraction).
+ * AUTO takes z when the box is longer in z than in x (the flow axis of a
+ * nozzle), else x. */
+enum { LBM_ROWS_AUTO = 0, LBM_ROWS_X = 1, LBM_ROWS_Z = 2 };
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -87,6 +92,7 @@ typedef struct {
     float fp16_scale;     /* FP16S scale s: a power of two > 0 (0 selects 4096 = 2^12, which keeps
                              deviations of 1e-4..10 in the normal FP16 range) */
     int32_t device;       /* CUDA device ordinal */
+    int32_t row_axis;     /* LBM_ROWS_AUTO (0), LBM_ROWS_X or LBM_ROWS_Z */
     void *stream;         /* cudaStream_t for all work of this context (NULL: default stream) */
     lbm_allocator allocator;
 } lbm_desc;
@@ -147,15 +153,17 @@ lbm_status lbm_make_nozzle(int32_t D, int32_t d, int32_t L_in, int32_t L_cone, i
                            int32_t L_total, double half_angle_deg, uint8_t *out);
 
 /* Host-only check of a flag field (no device needed): builds the sparse index
- * exactly as lbm_set_geometry would and re-verifies, independently, the
- * invariants the kernels rely on (every staged copy 16-byte aligned and inside
- * its buffer, every fluid cell in exactly one work unit, every pull slot
- * stored).  out (may be NULL) receives: active cells, storage slots, fluid
- * segments, fluid chunks, inlet/outlet nodes, wall links, rows, 0.
+ * exactly as lbm_set_geometry would with rows along row_axis (LBM_ROWS_*) and
+ * re-verifies, independently, the invariants the kernels rely on (every
+ * chunk lane a unique fluid cell, every position the step touches owning its
+ * slot, every pull slot inside the buffer and stored).  out (may be NULL)
+ * receives: active cells, storage slots, row records, fluid chunks,
+ * inlet/outlet nodes, wall links, rows, row axis used (LBM_ROWS_X or _Z).
  * Errors: LBM_ERR_ARG (inconsistent flag field, same rules as
- * lbm_set_geometry), LBM_ERR_STATE (an index invariant does not hold). */
+ * lbm_set_geometry; bad row_axis), LBM_ERR_STATE (an index invariant does
+ * not hold). */
 lbm_status lbm_check_layout(const uint8_t *flags, int32_t nx, int32_t ny, int32_t nz, int32_t periodic,
-                            int64_t out[8]);
+                            int32_t row_axis, int64_t out[8]);
 
 /* Install the geometry: flags[nz][ny][nx] host array of LBM_SOLID / FLUID /
  * INLET / OUTLET (copied).  Builds the fluid-only sparse index (rows of

@@ -115,7 +115,7 @@ void dev_free(lbm_ctx *c, void *p, size_t bytes) {
 }
 
 size_t pop_bytes(const lbm_ctx *c) { return (size_t)27 * (size_t)c->idx.nslots * storage_bytes(c->desc.precision); }
-size_t margin_bytes(const lbm_ctx *c) { return (size_t)buffer_margin(c->desc.nx) * storage_bytes(c->desc.precision); }
+size_t margin_bytes(const lbm_ctx *c) { return (size_t)buffer_margin(c->idx.n_row) * storage_bytes(c->desc.precision); }
 size_t raw_pop_bytes(const lbm_ctx *c) { return pop_bytes(c) + 2 * margin_bytes(c); }
 size_t raw_mask_bytes(const lbm_ctx *c) { return ((size_t)c->idx.nslots + 2 * MASK_MARGIN) * 4; }
 
@@ -189,11 +189,16 @@ lbm_status need(lbm_ctx *c, bool geom, bool params, bool state) {
     return LBM_OK;
 }
 
+// Whether the row axis of the context's index is periodic.
+int periodic_rows(const lbm_ctx *c) {
+    return (c->desc.periodic & (c->idx.row_axis == 2 ? LBM_PERIODIC_Z : LBM_PERIODIC_X)) ? 1 : 0;
+}
+
 // Ghost slots and periodic copies of the current buffer from its active cells.
 cudaError_t fill_ghosts(lbm_ctx *c) {
     return DISPATCH(c->desc.precision, launch_fill_ghosts, c->f[c->cur], c->d_mask, c->d_chunks, c->d_row_nb,
                     (int32_t)c->idx.chunks.size(), c->d_bnodes, (int32_t)c->idx.bnodes.size(), c->idx.nslots,
-                    c->desc.nx, (c->desc.periodic & LBM_PERIODIC_X) ? 1 : 0, c->stream);
+                    c->idx.n_row, periodic_rows(c), c->idx.row_axis, c->stream);
 }
 
 lbm_status reset_state(lbm_ctx *c) {
@@ -227,8 +232,10 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.nx = c->desc.nx;
     a.ny = c->desc.ny;
     a.nz = c->desc.nz;
-    a.ny_e = c->idx.ny_e;
-    a.periodic_x = (c->desc.periodic & LBM_PERIODIC_X) ? 1 : 0;
+    a.na_e = c->idx.na_e;
+    a.n_row = c->idx.n_row;
+    a.row_axis = c->idx.row_axis;
+    a.periodic_row = periodic_rows(c);
     a.profile = c->params.inlet_profile;
     a.inlet_ramp = c->params.inlet_ramp;
     const double gr[4] = {c->params.omega3, c->params.omega4, c->params.omega5, c->params.omega6};
@@ -327,6 +334,8 @@ lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out) {
     if (desc->precision < LBM_FP64 || desc->precision > LBM_FP16S) return LBM_ERR_ARG;
     if (desc->periodic & ~7) return LBM_ERR_ARG;
     if ((desc->allocator.alloc == nullptr) != (desc->allocator.free == nullptr)) return LBM_ERR_ARG;
+    if (desc->row_axis != LBM_ROWS_AUTO && desc->row_axis != LBM_ROWS_X && desc->row_axis != LBM_ROWS_Z)
+        return LBM_ERR_ARG;
     const float s = resolve_fp16_scale(desc->fp16_scale);
     if (s == 0.0f) return LBM_ERR_ARG;
     int ndev = 0;
@@ -393,7 +402,7 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     }
     // cells with at least one interpolated link leave the chunk lanes for the
     // wall kernel's list (slot order)
-    const int ny_e = c->idx.ny_e;
+    const bool zrows = c->idx.row_axis == 2;
     std::vector<int4> wn;
     std::vector<int2> chunks = c->idx.chunks;
     std::vector<char> is_wall((size_t)c->idx.nslots, 0);
@@ -404,9 +413,11 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
         const int64_t b = cells[r];
         const int x = (int)(b % c->desc.nx), y = (int)((b / c->desc.nx) % c->desc.ny);
         const int z = (int)(b / ((int64_t)c->desc.nx * c->desc.ny));
-        const int row = (y + 1) + ny_e * (z + 1);
+        // storage coordinates: p along the rows, (a, b) across them
+        const int p = zrows ? z : x, ra = zrows ? x : y, rb = zrows ? y : z;
+        const int row = (ra + 1) + c->idx.na_e * (rb + 1);
         const int32_t slot = c->idx.slot_of_active[(size_t)active_of_box[(size_t)b]];
-        wn.push_back(make_int4(x, row, slot, (int)r));
+        wn.push_back(make_int4(p, row, slot, (int)r));
         is_wall[(size_t)slot] = 1;
     }
     std::sort(wn.begin(), wn.end(), [](const int4 &p, const int4 &q2) { return p.z < q2.z; });
@@ -457,7 +468,8 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *flags) {
     if (!c) return LBM_ERR_ARG;
     if (!flags) return fail(c, LBM_ERR_ARG, "flags is NULL");
     HostIndex idx;
-    std::string msg = build_index(flags, c->desc.nx, c->desc.ny, c->desc.nz, c->desc.periodic, idx);
+    std::string msg = build_index(flags, c->desc.nx, c->desc.ny, c->desc.nz, c->desc.periodic, idx, 0,
+                                  c->desc.row_axis);
     if (!msg.empty()) return fail(c, LBM_ERR_ARG, msg);
     return lbm::ctx_install_index(c, std::move(idx));
 }
@@ -468,7 +480,7 @@ namespace lbm {
 
 int64_t ctx_footprint(const lbm_desc &d, const HostIndex &ix) {
     const int S = storage_bytes(d.precision);
-    const int64_t pop = 27 * ix.nslots * S + 2 * buffer_margin(d.nx) * S;
+    const int64_t pop = 27 * ix.nslots * S + 2 * buffer_margin(ix.n_row) * S;
     const int64_t blocks = std::max<int64_t>(fluid_blocks((int32_t)ix.chunks.size()) + node_blocks((int64_t)ix.bnodes.size()),
                                              node_blocks(ix.n_active));
     return 2 * pop + (ix.nslots + 2 * MASK_MARGIN) * 4 + (int64_t)ix.row_nb.size() * 4 + (int64_t)ix.chunks.size() * 8 +

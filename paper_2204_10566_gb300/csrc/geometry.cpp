@@ -1,17 +1,23 @@
 // Host-side geometry: nozzle voxeliser and the fluid-only sparse index.
 //
-// Storage layout ("slots"): rows are the x-lines of the box extended by one
-// layer in y and z (row = (y+1) + (ny+2)(z+1)).  A row stores, x-contiguously,
-// every position that the step kernel reads or writes in it: its active
-// cells, the ghost positions of wall links (a solid or outside position
-// x - c_i next to an active fluid cell x) and, for a periodic x axis, the two
-// wrap-around copies at x = -1 and x = nx.  Each row's stored range is
-// rounded outward to CHUNK boundaries, so slot = base(row) + x with base a
-// multiple of CHUNK.  Solid cells inside a stored range are padding.
+// Storage layout ("slots"): rows are the lines of the box along one axis, the
+// row axis (x, or z for lattices longer in z than in x), over the box
+// extended by one layer in the two cross axes.  In storage coordinates
+// (p along the row axis, a and b across it; (p, a, b) = (x, y, z) for rows
+// along x and (z, x, y) for rows along z), row = (a+1) + (n_a+2)(b+1).  A row
+// stores, p-contiguously, every position that the step kernel reads or
+// writes in it: its active cells, the ghost positions of wall links (a solid
+// or outside position p - c_p next to an active fluid cell) and, for a
+// periodic row axis, the two wrap-around copies at p = -1 and p = n_p.  Each
+// row's stored range is rounded outward to CHUNK boundaries, so
+// slot = base(row) + p with base a multiple of CHUNK.  Solid cells inside a
+// stored range are padding.
 //
-// Because every pull source x - c_i has a slot (an active cell, a ghost slot
-// holding the reflected population, or a periodic copy), the kernel's gather
-// is branch-free: slot = nb[j] + x - cx, with nb the row's neighbour bases.
+// Because every pull source has a slot (an active cell, a ghost slot holding
+// the reflected population, or a periodic copy), the kernel's gather is
+// branch-free: slot = nb[j] + p - c_p, with nb the row's nine neighbour
+// bases, j = (c_a + 1) + 3 (c_b + 1).  Long rows (the flow axis of a nozzle)
+// leave few padding lanes and few row ends, where the pulls straddle sectors.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -27,8 +33,55 @@ static inline int64_t box_index(int x, int y, int z, int nx, int ny) {
     return (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
 }
 
+int choose_row_axis(int nx, int ny, int nz, int requested) {
+    (void)ny;
+    if (requested == LBM_ROWS_X) return 0;
+    if (requested == LBM_ROWS_Z) return 2;
+    return nz > nx ? 2 : 0;  // the longer of x and z
+}
+
+namespace {
+
+// Storage coordinates of a lattice whose rows run along axis ax (0: x, 2: z).
+struct Frame {
+    int ax, nx, ny, nz;
+    int np, na, nb;     // extents along the row, and across it
+    bool pp, pa, pb;    // periodic along the row, across it
+    Frame(int ax_, int nx_, int ny_, int nz_, int periodic) : ax(ax_), nx(nx_), ny(ny_), nz(nz_) {
+        const bool px = periodic & LBM_PERIODIC_X, py = periodic & LBM_PERIODIC_Y, pz = periodic & LBM_PERIODIC_Z;
+        if (ax == 0) {
+            np = nx, na = ny, nb = nz, pp = px, pa = py, pb = pz;
+        } else {
+            np = nz, na = nx, nb = ny, pp = pz, pa = px, pb = py;
+        }
+    }
+    // box index of storage position (p, a, b), all inside the box
+    int64_t box(int p, int a, int b) const {
+        return ax == 0 ? box_index(p, a, b, nx, ny) : box_index(a, b, p, nx, ny);
+    }
+    // storage position of physical cell (x, y, z)
+    void from_xyz(int x, int y, int z, int &p, int &a, int &b) const {
+        if (ax == 0) {
+            p = x, a = y, b = z;
+        } else {
+            p = z, a = x, b = y;
+        }
+    }
+    // storage components of direction i (physical c = (i%3-1, (i/3)%3-1, i/9-1))
+    void dir(int i, int &cp, int &ca, int &cb) const {
+        const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+        if (ax == 0) {
+            cp = cx, ca = cy, cb = cz;
+        } else {
+            cp = cz, ca = cx, cb = cy;
+        }
+    }
+};
+
+}  // namespace
+
 std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out,
-                        int64_t max_slots) {
+                        int64_t max_slots, int row_axis) {
     const int64_t ncell = (int64_t)nx * ny * nz;
     for (int64_t b = 0; b < ncell; ++b)
         if (flags[b] > LBM_OUTLET) {
@@ -37,63 +90,65 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                      (long long)b);
             return msg;
         }
-    if (nx > (int)CHUNK_X0_MASK) return "nx too large (at most 2^20 - 1)";
     out = HostIndex();
-    const bool px = periodic & LBM_PERIODIC_X, py = periodic & LBM_PERIODIC_Y, pz = periodic & LBM_PERIODIC_Z;
-    const int ny_e = ny + 2, nz_e = nz + 2;
-    const int64_t nrows = (int64_t)ny_e * nz_e;
+    const Frame F(choose_row_axis(nx, ny, nz, row_axis), nx, ny, nz, periodic);
+    if (F.np > (int)CHUNK_X0_MASK) return "lattice too long along its row axis (at most 2^20 - 1 cells)";
+    const int na_e = F.na + 2, nb_e = F.nb + 2;
+    const int64_t nrows = (int64_t)na_e * nb_e;
     if (nrows > INT32_MAX / 4) return "too many rows";
-    out.ny_e = ny_e;
-    out.nz_e = nz_e;
-    auto row_of = [&](int y, int z) -> int64_t { return (int64_t)(y + 1) + (int64_t)ny_e * (z + 1); };
-    // resolve a pull source (x, y, z) (each coordinate at most one step outside
-    // the box): returns its flag (SOLID when outside a non-periodic face) and
-    // the coordinates used for storage (y, z wrapped when periodic; x wrapped
-    // only for the flag lookup).
-    auto source = [&](int x, int y, int z, int &ys, int &zs) -> int {
+    out.row_axis = F.ax;
+    out.n_row = F.np;
+    out.na_e = na_e;
+    out.nb_e = nb_e;
+    auto row_of = [&](int a, int b) -> int64_t { return (int64_t)(a + 1) + (int64_t)na_e * (b + 1); };
+    // resolve a pull source (p, a, b) (each coordinate at most one step
+    // outside the box): returns its flag (SOLID when outside a non-periodic
+    // face) and the cross coordinates used for storage (wrapped when
+    // periodic; p is wrapped only for the flag lookup).
+    auto source = [&](int p, int a, int b, int &as, int &bs) -> int {
         bool outside = false;
-        int xw = x, yw = y, zw = z;
-        if (x < 0 || x >= nx) { if (px) xw = (x + nx) % nx; else outside = true; }
-        if (y < 0 || y >= ny) { if (py) yw = (y + ny) % ny; else outside = true; }
-        if (z < 0 || z >= nz) { if (pz) zw = (z + nz) % nz; else outside = true; }
-        ys = py ? yw : y;
-        zs = pz ? zw : z;
+        int pw = p, aw = a, bw = b;
+        if (p < 0 || p >= F.np) { if (F.pp) pw = (p + F.np) % F.np; else outside = true; }
+        if (a < 0 || a >= F.na) { if (F.pa) aw = (a + F.na) % F.na; else outside = true; }
+        if (b < 0 || b >= F.nb) { if (F.pb) bw = (b + F.nb) % F.nb; else outside = true; }
+        as = F.pa ? aw : a;
+        bs = F.pb ? bw : b;
         if (outside) return LBM_SOLID;
-        return flags[box_index(xw, yw, zw, nx, ny)];
+        return flags[F.box(pw, aw, bw)];
     };
 
     std::vector<int> need_lo((size_t)nrows, INT_MAX), need_hi((size_t)nrows, INT_MIN);
     std::vector<int> act_lo((size_t)nrows, INT_MAX), act_hi((size_t)nrows, INT_MIN);  // fluid cells
-    auto need = [&](int64_t r, int x) {
-        if (x < need_lo[r]) need_lo[r] = x;
-        if (x > need_hi[r]) need_hi[r] = x;
+    auto need = [&](int64_t r, int p) {
+        if (p < need_lo[r]) need_lo[r] = p;
+        if (p > need_hi[r]) need_hi[r] = p;
     };
-    for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const int fl = flags[box_index(x, y, z, nx, ny)];
+    for (int b = 0; b < F.nb; ++b)
+        for (int a = 0; a < F.na; ++a)
+            for (int p = 0; p < F.np; ++p) {
+                const int fl = flags[F.box(p, a, b)];
                 if (fl == LBM_SOLID) continue;
-                const int64_t r = row_of(y, z);
-                need(r, x);
+                const int64_t r = row_of(a, b);
+                need(r, p);
                 if (fl == LBM_FLUID) {
-                    if (x < act_lo[r]) act_lo[r] = x;
-                    if (x > act_hi[r]) act_hi[r] = x;
+                    if (p < act_lo[r]) act_lo[r] = p;
+                    if (p > act_hi[r]) act_hi[r] = p;
                 }
-                if (px && x == nx - 1) need(r, -1);
-                if (px && x == 0) need(r, nx);
+                if (F.pp && p == F.np - 1) need(r, -1);
+                if (F.pp && p == 0) need(r, F.np);
                 if (fl != LBM_FLUID) continue;
                 for (int i = 0; i < 27; ++i) {
-                    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-                    int ys, zs;
-                    if (source(x - cx, y - cy, z - cz, ys, zs) == LBM_SOLID) need(row_of(ys, zs), x - cx);
+                    int cp, ca, cb, as, bs;
+                    F.dir(i, cp, ca, cb);
+                    if (source(p - cp, a - ca, b - cb, as, bs) == LBM_SOLID) need(row_of(as, bs), p - cp);
                 }
             }
     std::vector<int32_t> base((size_t)nrows, 0);
-    // Storage starts nx + 8 slots in: every chunk lane (fluid or not) then pulls
-    // from a non-negative slot, so the 32-bit unsigned element offsets of the
-    // step kernel never wrap (a non-fluid lane may pull from before the first
-    // stored cell of a neighbour row).
-    int64_t next = ((int64_t)nx + 8 + CHUNK - 1) / CHUNK * CHUNK;
+    // Storage starts n_p + 8 slots in: every chunk lane (fluid or not) then
+    // pulls from a non-negative slot, so the 32-bit unsigned element offsets
+    // of the step kernel never wrap (a non-fluid lane may pull from before the
+    // first stored cell of a neighbour row).
+    int64_t next = ((int64_t)F.np + 8 + CHUNK - 1) / CHUNK * CHUNK;
     for (int64_t r = 0; r < nrows; ++r) {
         if (need_lo[r] == INT_MAX) continue;
         const int lo = (int)std::floor(need_lo[r] / (double)CHUNK) * CHUNK;
@@ -111,43 +166,36 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
     }
     out.mask.assign((size_t)out.nslots, (uint32_t)TYPE_PAD << TYPE_SHIFT);
     out.row_nb.assign((size_t)nrows * ROW_RECORD_INTS, 0);
-    for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y) {
-            const int64_t r = row_of(y, z);
+    for (int b = 0; b < F.nb; ++b)
+        for (int a = 0; a < F.na; ++a) {
+            const int64_t r = row_of(a, b);
             if (need_lo[r] == INT_MAX) continue;
             for (int j = 0; j < 9; ++j) {
-                const int cy = j % 3 - 1, cz = j / 3 - 1;
-                int yy = y - cy, zz = z - cz;
-                if (py) yy = (yy + ny) % ny;
-                if (pz) zz = (zz + nz) % nz;
-                out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(yy, zz)];
-            }
-            if (act_lo[r] == INT_MAX) continue;
-            for (int x0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; x0 <= act_hi[r]; x0 += CHUNK) {
-                uint32_t lanes = 0;
-                for (int l = 0; l < CHUNK; ++l) {
-                    const int x = x0 + l;
-                    if (x < nx && flags[box_index(x, y, z, nx, ny)] == LBM_FLUID) lanes |= 1u << l;
-                }
-                out.chunks.push_back(make_int2((int)r, (int)((uint32_t)x0 | (lanes << CHUNK_LANES_SHIFT))));
+                const int ca = j % 3 - 1, cb = j / 3 - 1;
+                int aa = a - ca, bb = b - cb;
+                if (F.pa) aa = (aa + F.na) % F.na;
+                if (F.pb) bb = (bb + F.nb) % F.nb;
+                out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(aa, bb)];
             }
         }
-    if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
 
+    // link words, inlet/outlet nodes and the active order (increasing box index)
     static const int dirs[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
-                const int64_t b = box_index(x, y, z, nx, ny);
-                const int fl = flags[b];
+                const int64_t bx = box_index(x, y, z, nx, ny);
+                const int fl = flags[bx];
                 if (fl == LBM_SOLID) continue;
-                const int32_t slot = base[row_of(y, z)] + x;
+                int p, a, b;
+                F.from_xyz(x, y, z, p, a, b);
+                const int32_t slot = base[row_of(a, b)] + p;
                 uint32_t m = 0, type = TYPE_FLUID, dir = 0;
                 if (fl == LBM_FLUID) {
                     for (int i = 0; i < 27; ++i) {
-                        const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-                        int ys, zs;
-                        if (source(x - cx, y - cy, z - cz, ys, zs) == LBM_SOLID) {
+                        int cp, ca, cb, as, bs;
+                        F.dir(i, cp, ca, cb);
+                        if (source(p - cp, a - ca, b - cb, as, bs) == LBM_SOLID) {
                             m |= 1u << i;
                             ++out.n_ghost;
                         }
@@ -156,8 +204,9 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                     type = fl == LBM_INLET ? TYPE_INLET : TYPE_OUTLET;
                     int count = 0;
                     for (int k = 0; k < 6; ++k) {
-                        int ys, zs;
-                        if (source(x + dirs[k][0], y + dirs[k][1], z + dirs[k][2], ys, zs) == LBM_FLUID) {
+                        int dp, da, db, as, bs;
+                        F.from_xyz(dirs[k][0], dirs[k][1], dirs[k][2], dp, da, db);
+                        if (source(p + dp, a + da, b + db, as, bs) == LBM_FLUID) {
                             ++count;
                             dir = (uint32_t)k;
                         }
@@ -172,87 +221,124 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
                 }
                 out.mask[(size_t)slot] = m | (type << TYPE_SHIFT) | (dir << DIR_SHIFT);
                 if (type != TYPE_FLUID)
-                    out.bnodes.push_back(make_int4(x, (int)row_of(y, z), slot, (int)out.mask[(size_t)slot]));
+                    out.bnodes.push_back(make_int4(p, (int)row_of(a, b), slot, (int)out.mask[(size_t)slot]));
                 out.slot_of_active.push_back(slot);
-                out.box_of_active.push_back(b);
+                out.box_of_active.push_back(bx);
             }
     out.n_active = (int64_t)out.slot_of_active.size();
     if (out.n_active == 0) return "geometry has no active cells";
 
     // Non-active slots: bit i marks population array i as read there (the
-    // ghost slot of a wall link, or a periodic-x copy).  The fluid kernel
-    // writes every other array of a non-fluid chunk lane with filler, so that
-    // the 32-byte sectors at row ends are written whole.
-    for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const int fl = flags[box_index(x, y, z, nx, ny)];
+    // ghost slot of a wall link, or a periodic copy along the rows).  The
+    // fluid kernel writes every other array of a non-fluid chunk lane with
+    // filler, so that the 32-byte sectors at row ends are written whole.
+    for (int b = 0; b < F.nb; ++b)
+        for (int a = 0; a < F.na; ++a)
+            for (int p = 0; p < F.np; ++p) {
+                const int fl = flags[F.box(p, a, b)];
                 if (fl == LBM_SOLID) continue;
-                const int64_t r = row_of(y, z);
-                if (px && x == nx - 1)
-                    for (int i = 2; i < 27; i += 3) out.mask[(size_t)(base[r] - 1)] |= 1u << i;
-                if (px && x == 0)
-                    for (int i = 0; i < 27; i += 3) out.mask[(size_t)(base[r] + nx)] |= 1u << i;
-                if (fl != LBM_FLUID) continue;
+                const int64_t r = row_of(a, b);
                 for (int i = 0; i < 27; ++i) {
-                    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-                    int ys, zs;
-                    if (source(x - cx, y - cy, z - cz, ys, zs) == LBM_SOLID)
-                        out.mask[(size_t)(base[row_of(ys, zs)] + x - cx)] |= 1u << i;
+                    int cp, ca, cb, as, bs;
+                    F.dir(i, cp, ca, cb);
+                    if (F.pp && p == F.np - 1 && cp == 1) out.mask[(size_t)(base[r] - 1)] |= 1u << i;
+                    if (F.pp && p == 0 && cp == -1) out.mask[(size_t)(base[r] + F.np)] |= 1u << i;
+                    if (fl == LBM_FLUID && source(p - cp, a - ca, b - cb, as, bs) == LBM_SOLID)
+                        out.mask[(size_t)(base[row_of(as, bs)] + p - cp)] |= 1u << i;
                 }
             }
+
+    // Chunk records over each row's fluid cells.  A chunk whose eight slots
+    // hold no fluid cell and nothing that is read (a solid stretch inside a
+    // row's stored range) is left out.
+    for (int b = 0; b < F.nb; ++b)
+        for (int a = 0; a < F.na; ++a) {
+            const int64_t r = row_of(a, b);
+            if (act_lo[r] == INT_MAX) continue;
+            for (int p0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; p0 <= act_hi[r]; p0 += CHUNK) {
+                uint32_t lanes = 0, read = 0;
+                for (int l = 0; l < CHUNK; ++l) {
+                    const int p = p0 + l;
+                    if (p < F.np && flags[F.box(p, a, b)] == LBM_FLUID) lanes |= 1u << l;
+                    const uint32_t m = out.mask[(size_t)(base[r] + p)];
+                    if (((m >> TYPE_SHIFT) & 3u) != TYPE_PAD || (m & LINK_MASK)) read |= 1u << l;
+                }
+                if (!lanes && !read) continue;
+                out.chunks.push_back(make_int2((int)r, (int)((uint32_t)p0 | (lanes << CHUNK_LANES_SHIFT))));
+            }
+        }
+    if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
     return "";
 }
 
 // Structural invariants of an index, re-derived independently of how
-// build_index produced it: segment and chunk records, alignment and bounds of
-// every staged copy, and the pull slot of every link of every fluid cell.
+// build_index produced it: chunk records, alignment and bounds of every
+// slot the kernels touch, and the pull slot of every link of every fluid
+// cell.  Positions are written in storage coordinates (p along the row
+// axis, a and b across it) with their own mapping from the box.
 std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, int ny, int nz, int periodic) {
     const int64_t ns = ix.nslots;
-    const int64_t nrows = (int64_t)ix.ny_e * ix.nz_e;
+    const bool zrows = ix.row_axis == 2;
+    if (ix.row_axis != 0 && !zrows) return "row axis";
+    const int np = zrows ? nz : nx, na = zrows ? nx : ny, nb = zrows ? ny : nz;
+    const bool px = periodic & LBM_PERIODIC_X, py = periodic & LBM_PERIODIC_Y, pz = periodic & LBM_PERIODIC_Z;
+    const bool pp = zrows ? pz : px, pa = zrows ? px : py, pb = zrows ? py : pz;
+    if (ix.n_row != np || ix.na_e != na + 2 || ix.nb_e != nb + 2) return "row grid";
+    const int64_t nrows = (int64_t)ix.na_e * ix.nb_e;
     if (ix.row_nb.size() != (size_t)nrows * ROW_RECORD_INTS) return "row record count";
+    // box index of storage position (p, a, b) inside the box, and back
+    auto box_of = [&](int p, int a, int b) -> int64_t {
+        const int x = zrows ? a : p, y = zrows ? b : a, z = zrows ? p : b;
+        return (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
+    };
+    auto pab_of = [&](int64_t bx, int &p, int &a, int &b) {
+        const int x = (int)(bx % nx), y = (int)((bx / nx) % ny), z = (int)(bx / ((int64_t)nx * ny));
+        p = zrows ? z : x;
+        a = zrows ? x : y;
+        b = zrows ? y : z;
+    };
     std::vector<uint8_t> seen((size_t)nx * ny * nz, 0);
 
     for (const int2 &c : ix.chunks) {
-        const int r = c.x, x0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
+        const int r = c.x, p0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
         const uint32_t lanes = ((uint32_t)c.y >> CHUNK_LANES_SHIFT) & 0xFFu;
-        if (r < 0 || r >= nrows || x0 % CHUNK) return "bad chunk";
+        if (r < 0 || r >= nrows || p0 % CHUNK) return "bad chunk";
         for (int j = 0; j < 9; ++j)
             if (ix.row_nb[(size_t)r * ROW_RECORD_INTS + j] % CHUNK) return "row base not chunk aligned";
-        const int y = r % ix.ny_e - 1, z = r / ix.ny_e - 1;
+        const int a = r % ix.na_e - 1, b = r / ix.na_e - 1;
         for (int l = 0; l < CHUNK; ++l) {
             if (!((lanes >> l) & 1u)) continue;
-            const int x = x0 + l;
-            if (x >= nx) return "chunk lane outside the box";
-            const int64_t bx = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
+            const int p = p0 + l;
+            if (p >= np || a < 0 || a >= na || b < 0 || b >= nb) return "chunk lane outside the box";
+            const int64_t bx = box_of(p, a, b);
             if (flags[bx] != LBM_FLUID || seen[bx]++) return "chunk lane is not a unique fluid cell";
         }
     }
     // Every position the step reads or writes owns its slot: the active
-    // cells, their periodic-x copies, and the ghost position of every wall
-    // link (x - c_i in the pulled row; rows wrap on periodic y / z faces).
-    // Two positions sharing a slot (overlapping row ranges, a missing copy)
-    // would overwrite each other.
-    const bool px = periodic & LBM_PERIODIC_X, py = periodic & LBM_PERIODIC_Y, pz = periodic & LBM_PERIODIC_Z;
+    // cells, their periodic copies along the rows, and the ghost position of
+    // every wall link (p - c_p in the pulled row; rows wrap on periodic cross
+    // faces).  Two positions sharing a slot (overlapping row ranges, a missing
+    // copy) would overwrite each other.
     std::vector<int32_t> slot_of_box((size_t)nx * ny * nz, -1);
     std::vector<int64_t> owner((size_t)ns, -1);
-    const int64_t width = (int64_t)nx + 2;  // positions -1 .. nx of a row
-    auto row_e = [&](int y, int z) -> int64_t { return (int64_t)(y + 1) + (int64_t)ix.ny_e * (z + 1); };
-    auto claim = [&](int64_t row, int x, int64_t s) -> bool {
+    const int64_t width = (int64_t)np + 2;  // positions -1 .. np of a row
+    auto row_e = [&](int a, int b) -> int64_t { return (int64_t)(a + 1) + (int64_t)ix.na_e * (b + 1); };
+    auto claim = [&](int64_t row, int p, int64_t s) -> bool {
         if (s < 0 || s >= ns) return false;
-        const int64_t key = row * width + (x + 1);
+        const int64_t key = row * width + (p + 1);
         int64_t &o = owner[(size_t)s];
         if (o < 0) o = key;
         return o == key;
     };
     for (int64_t k = 0; k < ix.n_active; ++k) {
         const int64_t bx = ix.box_of_active[k];
-        const int x = (int)(bx % nx), y = (int)((bx / nx) % ny), z = (int)(bx / ((int64_t)nx * ny));
-        const int32_t *nb = &ix.row_nb[(size_t)row_e(y, z) * ROW_RECORD_INTS];
+        int p, a, b;
+        pab_of(bx, p, a, b);
+        const int32_t *nb_ = &ix.row_nb[(size_t)row_e(a, b) * ROW_RECORD_INTS];
         slot_of_box[(size_t)bx] = ix.slot_of_active[k];
-        if (!claim(row_e(y, z), x, ix.slot_of_active[k])) return "two positions share the slot of an active cell";
-        if (px && x == nx - 1 && !claim(row_e(y, z), -1, (int64_t)nb[4] - 1)) return "periodic copy slot";
-        if (px && x == 0 && !claim(row_e(y, z), nx, (int64_t)nb[4] + nx)) return "periodic copy slot";
+        if (!claim(row_e(a, b), p, ix.slot_of_active[k])) return "two positions share the slot of an active cell";
+        if (pp && p == np - 1 && !claim(row_e(a, b), -1, (int64_t)nb_[4] - 1)) return "periodic copy slot";
+        if (pp && p == 0 && !claim(row_e(a, b), np, (int64_t)nb_[4] + np)) return "periodic copy slot";
     }
     // pulls of every fluid cell land on stored slots: exactly the slot of an
     // active source inside the box, else a non-active slot of the pulled
@@ -260,32 +346,34 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     for (int64_t k = 0; k < ix.n_active; ++k) {
         const int64_t bx = ix.box_of_active[k];
         if (flags[bx] != LBM_FLUID) continue;
-        const int x = (int)(bx % nx), y = (int)((bx / nx) % ny), z = (int)(bx / ((int64_t)nx * ny));
-        const int32_t *nb = &ix.row_nb[(size_t)row_e(y, z) * ROW_RECORD_INTS];
-        if (nb[4] + x != ix.slot_of_active[k]) return "slot of an active cell";
+        int p, a, b;
+        pab_of(bx, p, a, b);
+        const int32_t *nb_ = &ix.row_nb[(size_t)row_e(a, b) * ROW_RECORD_INTS];
+        if (nb_[4] + p != ix.slot_of_active[k]) return "slot of an active cell";
         for (int i = 0; i < 27; ++i) {
             const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-            const int64_t s = (int64_t)nb[i / 3] + x - cx;
+            const int cp = zrows ? cz : cx, ca = zrows ? cx : cy, cb = zrows ? cy : cz;
+            const int64_t s = (int64_t)nb_[(ca + 1) + 3 * (cb + 1)] + p - cp;
             if (s < 0 || s >= ns) return "pull slot outside the buffer";
             const uint32_t m = ix.mask[(size_t)s];
             if (((m >> TYPE_SHIFT) & 3u) == TYPE_PAD && !((m >> i) & 1u)) return "pulled slot not marked as read";
-            int xs = x - cx, ys = y - cy, zs = z - cz;
-            bool outside = false, wrapped_x = false;
-            if (xs < 0 || xs >= nx) {
-                if (px) { xs = (xs + nx) % nx; wrapped_x = true; } else outside = true;
+            int ps = p - cp, as = a - ca, bs = b - cb;
+            bool outside = false, wrapped_p = false;
+            if (ps < 0 || ps >= np) {
+                if (pp) { ps = (ps + np) % np; wrapped_p = true; } else outside = true;
             }
-            if (ys < 0 || ys >= ny) { if (py) ys = (ys + ny) % ny; else outside = true; }
-            if (zs < 0 || zs >= nz) { if (pz) zs = (zs + nz) % nz; else outside = true; }
-            if (!outside && !wrapped_x) {
-                const int32_t own = slot_of_box[(size_t)(xs + (int64_t)nx * (ys + (int64_t)ny * zs))];
+            if (as < 0 || as >= na) { if (pa) as = (as + na) % na; else outside = true; }
+            if (bs < 0 || bs >= nb) { if (pb) bs = (bs + nb) % nb; else outside = true; }
+            if (!outside && !wrapped_p) {
+                const int32_t own = slot_of_box[(size_t)box_of(ps, as, bs)];
                 if (own >= 0) {
                     if (s != own) return "pull of an active source misses its slot";
                     continue;
                 }
             }
-            // ghost of a wall link, or a periodic-x copy: the pulled row (wrapped
-            // on periodic y / z faces) at x - cx
-            if (!claim(row_e(py ? ys : y - cy, pz ? zs : z - cz), x - cx, s))
+            // ghost of a wall link, or a periodic copy: the pulled row (wrapped
+            // on periodic cross faces) at p - c_p
+            if (!claim(row_e(pa ? as : a - ca, pb ? bs : b - cb), p - cp, s))
                 return "two positions share a ghost or copy slot";
         }
     }
@@ -294,16 +382,18 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     // every lane of every chunk (fluid or not) loads its 27 pull slots: they
     // must not precede the buffer (the step kernel's 32-bit offsets are
     // unsigned) nor pass the end of its margin
-    const int64_t margin = buffer_margin(nx);
+    const int64_t margin = buffer_margin(np);
     for (const int2 &c : ix.chunks) {
-        const int32_t *nb = &ix.row_nb[(size_t)c.x * ROW_RECORD_INTS];
-        const int x0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
+        const int32_t *nb_ = &ix.row_nb[(size_t)c.x * ROW_RECORD_INTS];
+        const int p0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
         for (int l = 0; l < CHUNK; ++l)
             for (int i = 0; i < 27; ++i) {
-                const int64_t s = (int64_t)nb[i / 3] + x0 + l - (i % 3 - 1);
+                const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+                const int cp = zrows ? cz : cx, ca = zrows ? cx : cy, cb = zrows ? cy : cz;
+                const int64_t s = (int64_t)nb_[(ca + 1) + 3 * (cb + 1)] + p0 + l - cp;
                 if (s < 0 || s >= ns + margin) return "chunk lane pull outside the buffer";
             }
-        if ((int64_t)nb[4] + x0 < 0 || (int64_t)nb[4] + x0 + CHUNK > ns) return "chunk slots outside the buffer";
+        if ((int64_t)nb_[4] + p0 < 0 || (int64_t)nb_[4] + p0 + CHUNK > ns) return "chunk slots outside the buffer";
     }
     for (const int4 &n : ix.bnodes)
         if (n.z < 0 || n.z >= ns || ix.row_nb[(size_t)n.y * ROW_RECORD_INTS + 4] + n.x != n.z) return "boundary node";
@@ -315,10 +405,11 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
 
 // Host-only check of a flag field and its sparse index (C ABI, lbm.h).
 extern "C" lbm_status lbm_check_layout(const uint8_t *flags, int32_t nx, int32_t ny, int32_t nz, int32_t periodic,
-                                       int64_t out[8]) {
+                                       int32_t row_axis, int64_t out[8]) {
     if (!flags || nx < 1 || ny < 1 || nz < 1 || (periodic & ~7)) return LBM_ERR_ARG;
+    if (row_axis != LBM_ROWS_AUTO && row_axis != LBM_ROWS_X && row_axis != LBM_ROWS_Z) return LBM_ERR_ARG;
     lbm::HostIndex ix;
-    if (!lbm::build_index(flags, nx, ny, nz, periodic, ix).empty()) return LBM_ERR_ARG;
+    if (!lbm::build_index(flags, nx, ny, nz, periodic, ix, 0, row_axis).empty()) return LBM_ERR_ARG;
     if (!lbm::validate_index(ix, flags, nx, ny, nz, periodic).empty()) return LBM_ERR_STATE;
     if (out) {
         out[0] = ix.n_active;
@@ -327,8 +418,8 @@ extern "C" lbm_status lbm_check_layout(const uint8_t *flags, int32_t nx, int32_t
         out[3] = (int64_t)ix.chunks.size();
         out[4] = (int64_t)ix.bnodes.size();
         out[5] = ix.n_ghost;
-        out[6] = (int64_t)ix.ny_e * ix.nz_e;
-        out[7] = 0;
+        out[6] = (int64_t)ix.na_e * ix.nb_e;
+        out[7] = ix.row_axis == 2 ? LBM_ROWS_Z : LBM_ROWS_X;
     }
     return LBM_OK;
 }

@@ -51,6 +51,12 @@
 #ifndef LBM_FUSE_BOUNDARY
 #define LBM_FUSE_BOUNDARY 1
 #endif
+// Warp-uniform fast path of the FP32 / FP16S fluid kernel for warps of fluid
+// cells without wall links (fluid_lane_voted); 0 runs every warp through the
+// general line sink.
+#ifndef LBM_FAST_PATH
+#define LBM_FAST_PATH 1
+#endif
 #ifndef LBM_STEP_MIN_BLOCKS_WALLQ
 #define LBM_STEP_MIN_BLOCKS_WALLQ 4
 #endif
@@ -112,6 +118,17 @@ struct Storage<2> {  // FP16 (f - w) * s, FP32 arithmetic
 __host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
 __host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
 __host__ __device__ constexpr int cz_of(int i) { return i / 9 - 1; }
+
+// Storage addressing of a lattice whose rows run along axis AX (0: x, 2: z):
+// the pull source of population i of the cell at row position p is slot
+// nb[row_line<AX>(i)] + p - c_row<AX>(i).
+template <int AX>
+__host__ __device__ constexpr int c_row(int i) { return AX == 0 ? cx_of(i) : cz_of(i); }
+template <int AX>
+__host__ __device__ constexpr int row_line(int i) { return AX == 0 ? i / 3 : (cx_of(i) + 1) + 3 * (cy_of(i) + 1); }
+// Population of storage line j with c_row = k - 1 (k = 0, 1, 2).
+template <int AX>
+__host__ __device__ constexpr int line_pop(int j, int k) { return AX == 0 ? 3 * j + k : j + 9 * k; }
 
 // 1-D Gauss-Hermite weights of the third-order quadrature (Appendix A).
 template <class R>
@@ -558,7 +575,7 @@ elem(int i, int64_t stride, int s) {
 // from slot nb[j] + x - cx of population array i.  For a wall link that slot
 // is the ghost slot holding f*_{26-i}(x) (halfway bounce-back, i.e.
 // Bouzidi's interpolated bounce-back at q = 1/2, Sec. 2.2).
-template <int P, bool WIDE, bool RAW = false>
+template <int P, bool WIDE, int AX, bool RAW = false>
 __device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], int x, typename Storage<P>::R (&d)[27]) {
     using S = Storage<P>;
     using T = typename S::T;
@@ -567,21 +584,26 @@ __device__ __forceinline__ void gather(const StepArgs &a, const int (&nb)[9], in
     const R inv_s = R(a.inv_scale);
 #if LBM_LINE_POINTERS
     if constexpr (!WIDE && P == 2) {
-        // one pointer per line j; the three pulls sit at +1, +stride, +2 stride - 1
+        // one pointer per storage line j (its three populations pull from
+        // row nb[j]); the pulls sit at +1, +(k1 - k0) stride, +(k2 - k0) stride - 1
         const uint32_t st = (uint32_t)a.stride;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const T *pj = fin + ((uint32_t)(3 * j) * st + (uint32_t)(nb[j] + x));
-            const T *q[3] = {pj + 1, pj + st, pj + 2 * st - 1};
+            constexpr int dk = line_pop<AX>(0, 1) - line_pop<AX>(0, 0);
+            const T *pj = fin + ((uint32_t)line_pop<AX>(j, 0) * st + (uint32_t)(nb[j] + x));
+            const T *q[3] = {pj + 1, pj + dk * st, pj + 2 * dk * st - 1};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) d[3 * j + c] = RAW ? S::load_raw(q[c]) : S::load(q[c], inv_s);
+            for (int k = 0; k < 3; ++k) {
+                const int i = line_pop<AX>(j, k);
+                d[i] = RAW ? S::load_raw(q[k]) : S::load(q[k], inv_s);
+            }
         }
         return;
     }
 #endif
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
-        const T *p = fin + elem<WIDE>(i, a.stride, nb[i / 3] + x - cx_of(i));
+        const T *p = fin + elem<WIDE>(i, a.stride, nb[row_line<AX>(i)] + x - c_row<AX>(i));
         d[i] = RAW ? S::load_raw(p) : S::load(p, inv_s);  // RAW: storage value, scale applied later
     }
 }
@@ -720,8 +742,9 @@ __device__ __forceinline__ void collide(typename Storage<P>::R (&d)[27], const F
 }
 
 // Post-collision state of one cell is in d; write it to its own slot, the
-// ghost slots of its wall links, and (periodic x) its wrap-around copies.
-template <int P, bool WIDE, bool RAW = false>
+// ghost slots of its wall links, and (periodic row axis) its wrap-around
+// copies.
+template <int P, bool WIDE, int AX, bool RAW = false>
 __device__ __forceinline__ void store_cell_state(const StepArgs &a, const int (&nb)[9], int x, int slot, uint32_t links,
                                                  const typename Storage<P>::R (&d)[27]) {
     using S0 = Storage<P>;
@@ -743,34 +766,38 @@ __device__ __forceinline__ void store_cell_state(const StepArgs &a, const int (&
     if (links) {  // wall links: the reflected population waits in the ghost slot
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            if (!(links & (7u << (3 * j)))) continue;  // no wall link towards row j
+            if (!(links & (7u << (3 * j)))) continue;  // no wall link among populations 3j .. 3j + 2
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int i = 3 * j + c;
-                if (links & (1u << i)) S::store(fout + elem<WIDE>(i, a.stride, nb[j] + x - cx_of(i)), d[26 - i], s);
+                if (links & (1u << i))
+                    S::store(fout + elem<WIDE>(i, a.stride, nb[row_line<AX>(i)] + x - c_row<AX>(i)), d[26 - i], s);
             }
         }
     }
-    if (a.periodic_x) {  // wrap-around copies read across the periodic x faces
-        if (x == a.nx - 1) {
+    if (a.periodic_row) {  // wrap-around copies read across the periodic faces of the row axis
+        if (x == a.n_row - 1) {
 #pragma unroll
-            for (int i = 2; i < 27; i += 3) S::store(fout + elem<WIDE>(i, a.stride, nb[4] - 1), d[i], s);
+            for (int i = 0; i < 27; ++i)
+                if (c_row<AX>(i) == 1) S::store(fout + elem<WIDE>(i, a.stride, nb[4] - 1), d[i], s);
         }
         if (x == 0) {
 #pragma unroll
-            for (int i = 0; i < 27; i += 3) S::store(fout + elem<WIDE>(i, a.stride, nb[4] + a.nx), d[i], s);
+            for (int i = 0; i < 27; ++i)
+                if (c_row<AX>(i) == -1) S::store(fout + elem<WIDE>(i, a.stride, nb[4] + a.n_row), d[i], s);
         }
     }
 }
 
 // Output sink of the fluid update: each line of three post-collision values
-// goes to the cell's own slots at once, to the ghost slots of the wall links
-// they serve (value i feeds link 26 - i), and across a periodic x face.
+// (populations 3j .. 3j + 2) goes to the cell's own slots at once, to the
+// ghost slots of the wall links they serve (value i feeds link 26 - i), and
+// across a periodic face of the row axis.
 // own: bit i set = store value i in the cell's own slot; bit 31 = the lane is
 // a fluid cell (the other lanes only fill unread arrays, see fluid_cell).
 constexpr uint32_t OWN_FLUID = 1u << 31;
 
-template <int P, bool WIDE, bool RAW>
+template <int P, bool WIDE, bool RAW, int AX>
 struct LineStore {
     using S = Storage<P>;
     using T = typename S::T;
@@ -817,12 +844,51 @@ struct LineStore {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int k = 26 - (3 * j + c);  // wall link k takes value 3j + c
-                if (links & (1u << k)) put(k, nb[k / 3] + x - cx_of(k), v[c]);
+                if (links & (1u << k)) put(k, nb[row_line<AX>(k)] + x - c_row<AX>(k), v[c]);
             }
         }
-        if (a.periodic_x && (own & OWN_FLUID)) {  // wrap-around copies read across the periodic x faces
-            if (x == a.nx - 1) put(3 * j + 2, nb[4] - 1, vp);
-            if (x == 0) put(3 * j, nb[4] + a.nx, vm);
+        if (a.periodic_row && (own & OWN_FLUID)) {  // wrap-around copies across the periodic row faces
+            const R v[3] = {vm, v0, vp};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int i = 3 * j + c;
+                if (c_row<AX>(i) == 1 && x == a.n_row - 1) put(i, nb[4] - 1, v[c]);
+                if (c_row<AX>(i) == -1 && x == 0) put(i, nb[4] + a.n_row, v[c]);
+            }
+        }
+    }
+};
+
+// Output sink of the fast path (a warp of fluid cells without wall links):
+// the 27 post-collision values go to the cell's own slots only, with no
+// predicate.  FP16S addresses each line's three stores from one pointer, FP32
+// by per-population offsets, as LineStore does.
+template <int P, bool RAW>
+struct OwnStore {
+    using S = Storage<P>;
+    using T = typename S::T;
+    using R = typename S::R;
+    const StepArgs &a;
+    int slot;
+    __device__ __forceinline__ void put(T *p, R v) const {
+        if constexpr (RAW)
+            S::store_raw(p, v);
+        else
+            S::store(p, v, R(a.scale));
+    }
+    __device__ __forceinline__ void moments(R omega, const R (&a2)[6]) const { record_stress(a, slot, omega, a2); }
+    __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const {
+        T *out = static_cast<T *>(a.fout);
+        const uint32_t st = (uint32_t)a.stride;
+        if constexpr (LBM_LINE_POINTERS && P == 2) {
+            T *pj = out + ((uint32_t)(3 * j) * st + (uint32_t)slot);
+            put(pj, vm);
+            put(pj + st, v0);
+            put(pj + 2 * st, vp);
+        } else {
+            put(out + elem<false>(3 * j, a.stride, slot), vm);
+            put(out + elem<false>(3 * j + 1, a.stride, slot), v0);
+            put(out + elem<false>(3 * j + 2, a.stride, slot), vp);
         }
     }
 };
@@ -856,7 +922,7 @@ __device__ __forceinline__ void record_cell(const StepArgs &a, int slot, R rho, 
 // there; nothing at inlet/outlet slots).  This completes the 32-byte sectors
 // at the row ends, which the memory system would otherwise have to read
 // back before writing them, at no extra instructions per warp.
-template <int P, bool GHOST1, bool WIDE, bool WALLQ>
+template <int P, bool GHOST1, bool WIDE, bool WALLQ, int AX>
 __device__ __forceinline__ void cell_update(const StepArgs &a, int row, int x, bool fluid, int qk, double (&hv)[6]) {
     using R = typename Storage<P>::R;
     int nb[9];
@@ -869,36 +935,84 @@ __device__ __forceinline__ void cell_update(const StepArgs &a, int row, int x, b
     R d[27];
     R rho, ux, uy, uz;
     constexpr bool RAW = GHOST1 && Storage<P>::SCALED;  // FP16 scale folded into the collision
-    gather<P, WIDE, RAW>(a, nb, x, d);
+    gather<P, WIDE, AX, RAW>(a, nb, x, d);
     if constexpr (WALLQ) interpolate_walls<P, WIDE, RAW>(a, qk, slot, links, d);
     if constexpr (GHOST1) {
-        const LineStore<P, WIDE, RAW> sink{a, nb, x, slot, links, own};
-        collide_ghost1<R, RAW, LineStore<P, WIDE, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
-                                                        R(a.scale), &sink);
+        const LineStore<P, WIDE, RAW, AX> sink{a, nb, x, slot, links, own};
+        collide_ghost1<R, RAW, LineStore<P, WIDE, RAW, AX>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
+                                                            R(a.scale), &sink);
     } else {
         if (!fluid) return;
         collide<P, GHOST1>(d, flow<R>(a), rho, ux, uy, uz, a, slot);
-        store_cell_state<P, WIDE, RAW>(a, nb, x, slot, links, d);
+        store_cell_state<P, WIDE, AX, RAW>(a, nb, x, slot, links, d);
     }
     if (fluid) record_cell(a, slot, rho, ux, uy, uz, hv);
 }
 
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, int AX>
 __device__ __forceinline__ void fluid_cell(const StepArgs &a, int chunk, int lane, double (&hv)[6]) {
     const int2 ch = __ldg(a.chunks + chunk);
     const uint32_t cw = (uint32_t)ch.y;
     const bool fluid = (cw >> (CHUNK_LANES_SHIFT + lane)) & 1u;
-    cell_update<P, GHOST1, WIDE, false>(a, ch.x, (int)(cw & CHUNK_X0_MASK) + lane, fluid, -1, hv);
+    cell_update<P, GHOST1, WIDE, false, AX>(a, ch.x, (int)(cw & CHUNK_X0_MASK) + lane, fluid, -1, hv);
+}
+
+// Fluid lane of the step kernel with a warp-uniform fast path (default ghost
+// rates, 32-bit offsets, FP32 / FP16S).  With rows along the flow axis most
+// warps hold 32 fluid cells none of which has a wall link (or, on a periodic
+// row axis, sits at a row end); such a warp stores every cell's 27 values
+// into its own slots and skips the line sink's per-value predicates,
+// ghost-slot stores and wrap-around copies.  The gather is the same on both paths, so it
+// is issued before the vote.  Every lane of the warp must call this (lanes
+// past the last chunk take part in the vote only).
+template <int P, int AX>
+__device__ __forceinline__ void fluid_lane_voted(const StepArgs &a, int chunk, int lane, double (&hv)[6]) {
+    using R = typename Storage<P>::R;
+    constexpr bool RAW = Storage<P>::SCALED;
+    const bool valid = chunk < a.nchunks;
+    int nb[9];
+    R d[27];
+    int x = 0, slot = 0;
+    uint32_t m = 0u;
+    bool fluid = false;
+    if (valid) {
+        const int2 ch = __ldg(a.chunks + chunk);
+        const uint32_t cw = (uint32_t)ch.y;
+        fluid = (cw >> (CHUNK_LANES_SHIFT + lane)) & 1u;
+        x = (int)(cw & CHUNK_X0_MASK) + lane;
+        load_row(a.row_nb, ch.x, nb);
+        slot = nb[4] + x;
+        gather<P, false, AX, RAW>(a, nb, x, d);
+        m = __ldg(a.mask + slot);
+    }
+    const bool row_end = a.periodic_row && (x == 0 || x == a.n_row - 1);  // writes wrap-around copies
+    const bool simple = fluid && (m & LINK_MASK) == 0u && !row_end;
+    const bool fast = __all_sync(0xffffffffu, simple);
+    if (!valid) return;
+    R rho, ux, uy, uz;
+    if (fast) {
+        const OwnStore<P, RAW> sink{a, slot};
+        collide_ghost1<R, RAW, OwnStore<P, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale), R(a.scale),
+                                                 &sink);
+    } else {
+        const uint32_t links = fluid ? (m & LINK_MASK) : 0u;
+        const uint32_t own = fluid ? (LINK_MASK | OWN_FLUID)
+                                   : (((m >> TYPE_SHIFT) & 3u) == TYPE_PAD ? (~m & LINK_MASK) : 0u);
+        const LineStore<P, false, RAW, AX> sink{a, nb, x, slot, links, own};
+        collide_ghost1<R, RAW, LineStore<P, false, RAW, AX>>(d, flow<R>(a).omega, rho, ux, uy, uz,
+                                                             R(a.inv_scale), R(a.scale), &sink);
+    }
+    if (fluid) record_cell(a, slot, rho, ux, uy, uz, hv);
 }
 
 // Update of wall cell k of the interpolated-wall list (x, row, slot, record):
 // the same update with Bouzidi's interpolation of its wall links.  These
 // cells are taken out of the chunk lanes while wall distances are set, so
 // the fluid kernel keeps its plain instruction stream.
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, int AX>
 __device__ __forceinline__ void wall_cell(const StepArgs &a, int k, double (&hv)[6]) {
     const int4 node = __ldg(a.wnodes + k);
-    cell_update<P, GHOST1, WIDE, true>(a, node.y, node.x, true, node.w, hv);
+    cell_update<P, GHOST1, WIDE, true, AX>(a, node.y, node.x, true, node.w, hv);
 }
 
 // Update of inlet/outlet node k: non-equilibrium extrapolation (Sec. 2.2)
@@ -906,25 +1020,29 @@ __device__ __forceinline__ void wall_cell(const StepArgs &a, int k, double (&hv)
 // same input state (so boundary and fluid updates are independent):
 //   f*_i(x_b) = f^eq_i(rho_b, u_b) + f*_i(x_f) - f^eq_i(rho_f, u_f),
 // inlet: rho_b = rho_f, u_b prescribed; outlet: rho_b = rho_out, u_b = u_f.
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, int AX>
 __device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (&hv)[6]) {
     using R = typename Storage<P>::R;
     const int4 node = __ldg(a.bnodes + k);
-    const int x = node.x, row = node.y, slot = node.z;
+    const int pos = node.x, row = node.y, slot = node.z;
     const uint32_t m = (uint32_t)node.w;
     const uint32_t type = (m >> TYPE_SHIFT) & 3u;
     const FlowParams<R> &fp = flow<R>(a);
-    const int y = row % a.ny_e - 1, z = row / a.ny_e - 1;
+    // box position from (row position, row): (p, a, b) = (x, y, z) or (z, x, y)
+    const int ra = row % a.na_e - 1, rb = row / a.na_e - 1;
+    const int x = AX == 0 ? pos : ra, y = AX == 0 ? ra : rb, z = AX == 0 ? rb : pos;
     const int dir = (int)(m >> DIR_SHIFT);
     const int nx_ = (dir == 0) - (dir == 1), ny_ = (dir == 2) - (dir == 3), nz_ = (dir == 4) - (dir == 5);
     const int xf = wrap(x + nx_, a.nx), yf = wrap(y + ny_, a.ny), zf = wrap(z + nz_, a.nz);
+    const int pf = AX == 0 ? xf : zf;  // the partner in storage coordinates
+    const int row_f = AX == 0 ? (yf + 1) + a.na_e * (zf + 1) : (xf + 1) + a.na_e * (yf + 1);
     int nbf[9];
-    load_row(a.row_nb, (yf + 1) + a.ny_e * (zf + 1), nbf);
+    load_row(a.row_nb, row_f, nbf);
     R d[27];
     R rf, uxf, uyf, uzf, rho, ux, uy, uz;
-    gather<P, WIDE>(a, nbf, xf, d);
+    gather<P, WIDE, AX>(a, nbf, pf, d);
     if (a.wall_qidx) {
-        const int sf = nbf[4] + xf;
+        const int sf = nbf[4] + pf;
         const uint32_t lf = __ldg(a.mask + sf) & LINK_MASK;
         if (lf) interpolate_walls<P, WIDE, false>(a, __ldg(a.wall_qidx + sf), sf, lf, d);
     }
@@ -962,7 +1080,7 @@ __device__ __forceinline__ void boundary_node(const StepArgs &a, int k, double (
     add_eq_difference<R>(rho, ux, uy, uz, rf, uxf, uyf, uzf, d);
     int nb[9];
     load_row(a.row_nb, row, nb);
-    store_cell_state<P, WIDE>(a, nb, x, slot, 0u, d);
+    store_cell_state<P, WIDE, AX>(a, nb, pos, slot, 0u, d);
     record_cell(a, slot, rho, ux, uy, uz, hv);
 }
 
@@ -977,14 +1095,14 @@ constexpr int64_t PREFETCH_MAX_BYTES = 16384;
 // is widened to 16-byte bounds, which stay inside the buffer margins.  Spans
 // that wrap around a periodic y or z face (reversed or very long) are
 // skipped: a prefetch only moves data, never changes a result.
-template <int P>
+template <int P, int AX>
 __device__ __forceinline__ void prefetch_block_sources(const StepArgs &a, int tb, int i) {
     using T = typename Storage<P>::T;
     const int c0 = tb * (STEP_THREADS / CHUNK);
     if (tb < 0 || c0 >= a.nchunks) return;
     const int c1 = min(c0 + STEP_THREADS / CHUNK, a.nchunks) - 1;
     const int2 h0 = __ldg(a.chunks + c0), h1 = __ldg(a.chunks + c1);
-    const int j = i / 3, cx = i % 3 - 1;
+    const int j = row_line<AX>(i), cx = c_row<AX>(i);
     const int *rn = reinterpret_cast<const int *>(a.row_nb);
     const int b0 = __ldg(rn + (int64_t)ROW_RECORD_INTS * h0.x + j);
     const int b1 = __ldg(rn + (int64_t)ROW_RECORD_INTS * h1.x + j);
@@ -1001,19 +1119,22 @@ __device__ __forceinline__ void prefetch_block_sources(const StepArgs &a, int tb
 // block also prefetches the pull sources of block blockIdx.x +
 // a.prefetch_ahead into L2 (one bulk prefetch per population), so that the
 // gathers of later blocks find their rows in L2 instead of waiting on HBM.
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, int AX>
 __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
     double hv[6] = {0, 0, 0, 0, 0, 0};
     if (LBM_FUSE_BOUNDARY && P == 1 && (int)blockIdx.x >= a.fluid_blocks) {  // inlet/outlet nodes, trailing blocks
         const int k = ((int)blockIdx.x - a.fluid_blocks) * STEP_THREADS + (int)threadIdx.x;
-        if (k < a.nbnodes) boundary_node<P, GHOST1, WIDE>(a, k, hv);
+        if (k < a.nbnodes) boundary_node<P, GHOST1, WIDE, AX>(a, k, hv);
     } else {
         const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
         const int chunk = gt / CHUNK;
-        if (chunk < a.nchunks) fluid_cell<P, GHOST1, WIDE>(a, chunk, gt % CHUNK, hv);
+        if constexpr (LBM_FAST_PATH && GHOST1 && !WIDE && P != 0)
+            fluid_lane_voted<P, AX>(a, chunk, gt % CHUNK, hv);  // every lane of the block calls it
+        else if (chunk < a.nchunks)
+            fluid_cell<P, GHOST1, WIDE, AX>(a, chunk, gt % CHUNK, hv);
         if (a.prefetch_ahead > 0) {
             const int i = (int)threadIdx.x - (STEP_THREADS - 32);
-            if (i >= 0 && i < 27) prefetch_block_sources<P>(a, (int)blockIdx.x + a.prefetch_ahead, i);
+            if (i >= 0 && i < 27) prefetch_block_sources<P, AX>(a, (int)blockIdx.x + a.prefetch_ahead, i);
         }
     }
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
@@ -1021,11 +1142,11 @@ __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS
 
 // One time step of the cells with interpolated walls (see wall_cell); its
 // partial sums follow those of the fluid and inlet/outlet kernels.
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, int AX>
 __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS_WALLQ) k_wall(const StepArgs a) {
     const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (k < a.nwnodes) wall_cell<P, GHOST1, WIDE>(a, k, hv);
+    if (k < a.nwnodes) wall_cell<P, GHOST1, WIDE, AX>(a, k, hv);
     if (a.flags & STEP_REDUCE) {
         const int before = a.fluid_blocks + (a.nbnodes + STEP_THREADS - 1) / STEP_THREADS;
         block_reduce_write(hv, a.partials + (size_t)before * REDUCE_SLOTS);
@@ -1034,11 +1155,11 @@ __global__ void __launch_bounds__(STEP_THREADS, P == 0 ? 1 : LBM_STEP_MIN_BLOCKS
 
 // One time step of every inlet/outlet node of one lattice (when they do not
 // ride in the trailing blocks of k_step).
-template <int P, bool GHOST1, bool WIDE>
+template <int P, bool GHOST1, bool WIDE, int AX>
 __global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
     const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (k < a.nbnodes) boundary_node<P, GHOST1, WIDE>(a, k, hv);
+    if (k < a.nbnodes) boundary_node<P, GHOST1, WIDE, AX>(a, k, hv);
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials + (size_t)a.fluid_blocks * REDUCE_SLOTS);
 }
 
@@ -1089,13 +1210,13 @@ __global__ void __launch_bounds__(STEP_THREADS) k_reduce(const void *f, const in
     block_reduce_write(hv, partials);
 }
 
-// Ghost slots and periodic-x copies of one buffer from its active cells:
-// the same writes the step kernel does after its collision, for a state set
-// from the host.
-template <int P>
+// Ghost slots and periodic copies along the rows of one buffer from its
+// active cells: the same writes the step kernel does after its collision,
+// for a state set from the host.
+template <int P, int AX>
 __global__ void __launch_bounds__(STEP_THREADS) k_fill_ghosts(void *f, const uint32_t *mask, const int2 *chunks,
                                                               const int4 *row_nb, int32_t nchunks, int64_t stride,
-                                                              int32_t nx, int32_t periodic_x) {
+                                                              int32_t n_row, int32_t periodic_row) {
     using T = typename Storage<P>::T;
     const int gt = blockIdx.x * STEP_THREADS + threadIdx.x;
     const int chunk = gt / CHUNK;
@@ -1112,21 +1233,25 @@ __global__ void __launch_bounds__(STEP_THREADS) k_fill_ghosts(void *f, const uin
     const uint32_t links = mask[slot] & LINK_MASK;
 #pragma unroll
     for (int i = 0; i < 27; ++i)
-        if (links & (1u << i)) p[(int64_t)i * stride + nb[i / 3] + x - cx_of(i)] = p[(int64_t)(26 - i) * stride + slot];
-    if (periodic_x) {
-        if (x == nx - 1)
+        if (links & (1u << i))
+            p[(int64_t)i * stride + nb[row_line<AX>(i)] + x - c_row<AX>(i)] = p[(int64_t)(26 - i) * stride + slot];
+    if (periodic_row) {
+        if (x == n_row - 1)
 #pragma unroll
-            for (int i = 2; i < 27; i += 3) p[(int64_t)i * stride + nb[4] - 1] = p[(int64_t)i * stride + slot];
+            for (int i = 0; i < 27; ++i)
+                if (c_row<AX>(i) == 1) p[(int64_t)i * stride + nb[4] - 1] = p[(int64_t)i * stride + slot];
         if (x == 0)
 #pragma unroll
-            for (int i = 0; i < 27; i += 3) p[(int64_t)i * stride + nb[4] + nx] = p[(int64_t)i * stride + slot];
+            for (int i = 0; i < 27; ++i)
+                if (c_row<AX>(i) == -1) p[(int64_t)i * stride + nb[4] + n_row] = p[(int64_t)i * stride + slot];
     }
 }
 
-// Periodic-x copies of the inlet/outlet nodes.
-template <int P>
+// Periodic copies along the rows of the inlet/outlet nodes.
+template <int P, int AX>
 __global__ void __launch_bounds__(STEP_THREADS) k_fill_periodic_nodes(void *f, const int4 *bnodes, int32_t nbnodes,
-                                                                      const int4 *row_nb, int64_t stride, int32_t nx) {
+                                                                      const int4 *row_nb, int64_t stride,
+                                                                      int32_t n_row) {
     using T = typename Storage<P>::T;
     const int k = blockIdx.x * STEP_THREADS + threadIdx.x;
     if (k >= nbnodes) return;
@@ -1134,12 +1259,14 @@ __global__ void __launch_bounds__(STEP_THREADS) k_fill_periodic_nodes(void *f, c
     const int x = node.x, slot = node.z;
     const int base = row_nb[3 * node.y + 1].x;
     T *p = static_cast<T *>(f);
-    if (x == nx - 1)
+    if (x == n_row - 1)
 #pragma unroll
-        for (int i = 2; i < 27; i += 3) p[(int64_t)i * stride + base - 1] = p[(int64_t)i * stride + slot];
+        for (int i = 0; i < 27; ++i)
+            if (c_row<AX>(i) == 1) p[(int64_t)i * stride + base - 1] = p[(int64_t)i * stride + slot];
     if (x == 0)
 #pragma unroll
-        for (int i = 0; i < 27; i += 3) p[(int64_t)i * stride + base + nx] = p[(int64_t)i * stride + slot];
+        for (int i = 0; i < 27; ++i)
+            if (c_row<AX>(i) == -1) p[(int64_t)i * stride + base + n_row] = p[(int64_t)i * stride + slot];
 }
 
 template <int P>
@@ -1225,11 +1352,11 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
     int per_sm = 0, sms = 0;
     cudaError_t e;
     if (ghost1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, true, true> : k_step<P, true, false>,
-                                                          STEP_THREADS, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, wide ? k_step<P, true, true, 0> : k_step<P, true, false, 0>, STEP_THREADS, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_step<P, false, true> : k_step<P, false, false>,
-                                                          STEP_THREADS, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, wide ? k_step<P, false, true, 0> : k_step<P, false, false, 0>, STEP_THREADS, 0);
     if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -1238,30 +1365,31 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
     return (int)((int64_t)per_sm * sms * pct / 100);
 }
 
-template <int P, bool G, bool WD>
-void launch_fluid(const StepArgs &a, cudaStream_t s) {
-    const int bb = LBM_FUSE_BOUNDARY && P == 1 ? (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS) : 0;
-    k_step<P, G, WD><<<step_blocks(a.nchunks) + bb, STEP_THREADS, 0, s>>>(a);
+template <int P, bool G, bool WD, int AX>
+void launch_step_ax(const StepArgs &a, cudaStream_t s) {
+    const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
+    const bool fused = LBM_FUSE_BOUNDARY && P == 1 && a.nchunks > 0;  // nodes in trailing blocks of k_step
+    if (a.nchunks > 0) k_step<P, G, WD, AX><<<step_blocks(a.nchunks) + (fused ? bb : 0), STEP_THREADS, 0, s>>>(a);
     if (a.nwnodes > 0)  // cells with interpolated walls
-        k_wall<P, G, WD><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
+        k_wall<P, G, WD, AX><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
+    if (bb > 0 && !fused) k_boundary<P, G, WD, AX><<<bb, STEP_THREADS, 0, s>>>(a);
+}
+
+template <int P, bool G, bool WD>
+void launch_step_rows(const StepArgs &a, cudaStream_t s) {
+    if (a.row_axis == 2)
+        launch_step_ax<P, G, WD, 2>(a, s);
+    else
+        launch_step_ax<P, G, WD, 0>(a, s);
 }
 
 template <int P>
 cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s) {
     const bool wide = a.wide_offsets || a.stride > MAX_SLOTS_32;
-    const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
-    if (a.nchunks > 0) {
-        if (ghost1)
-            wide ? launch_fluid<P, true, true>(a, s) : launch_fluid<P, true, false>(a, s);
-        else
-            wide ? launch_fluid<P, false, true>(a, s) : launch_fluid<P, false, false>(a, s);
-    }
-    if (bb > 0 && !(LBM_FUSE_BOUNDARY && P == 1 && a.nchunks > 0)) {
-        if (ghost1)
-            wide ? k_boundary<P, true, true><<<bb, STEP_THREADS, 0, s>>>(a) : k_boundary<P, true, false><<<bb, STEP_THREADS, 0, s>>>(a);
-        else
-            wide ? k_boundary<P, false, true><<<bb, STEP_THREADS, 0, s>>>(a) : k_boundary<P, false, false><<<bb, STEP_THREADS, 0, s>>>(a);
-    }
+    if (ghost1)
+        wide ? launch_step_rows<P, true, true>(a, s) : launch_step_rows<P, true, false>(a, s);
+    else
+        wide ? launch_step_rows<P, false, true>(a, s) : launch_step_rows<P, false, false>(a, s);
     return cudaGetLastError();
 }
 
@@ -1274,16 +1402,27 @@ cudaError_t launch_reduce(const void *f, const int32_t *slot_of_active, int64_t 
     return cudaGetLastError();
 }
 
-template <int P>
-cudaError_t launch_fill_ghosts(void *f, const uint32_t *mask, const int2 *chunks, const int4 *row_nb,
-                               int32_t nchunks, const int4 *bnodes, int32_t nbnodes, int64_t stride, int32_t nx,
-                               int32_t periodic_x, cudaStream_t s) {
+template <int P, int AX>
+void launch_fill_ghosts_ax(void *f, const uint32_t *mask, const int2 *chunks, const int4 *row_nb, int32_t nchunks,
+                           const int4 *bnodes, int32_t nbnodes, int64_t stride, int32_t n_row, int32_t periodic_row,
+                           cudaStream_t s) {
     const int blocks = step_blocks(nchunks);
     if (blocks > 0)
-        k_fill_ghosts<P><<<blocks, STEP_THREADS, 0, s>>>(f, mask, chunks, row_nb, nchunks, stride, nx, periodic_x);
-    if (periodic_x && nbnodes > 0)
-        k_fill_periodic_nodes<P><<<(nbnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(
-            f, bnodes, nbnodes, row_nb, stride, nx);
+        k_fill_ghosts<P, AX><<<blocks, STEP_THREADS, 0, s>>>(f, mask, chunks, row_nb, nchunks, stride, n_row,
+                                                             periodic_row);
+    if (periodic_row && nbnodes > 0)
+        k_fill_periodic_nodes<P, AX><<<(nbnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(
+            f, bnodes, nbnodes, row_nb, stride, n_row);
+}
+
+template <int P>
+cudaError_t launch_fill_ghosts(void *f, const uint32_t *mask, const int2 *chunks, const int4 *row_nb,
+                               int32_t nchunks, const int4 *bnodes, int32_t nbnodes, int64_t stride, int32_t n_row,
+                               int32_t periodic_row, int32_t row_axis, cudaStream_t s) {
+    if (row_axis == 2)
+        launch_fill_ghosts_ax<P, 2>(f, mask, chunks, row_nb, nchunks, bnodes, nbnodes, stride, n_row, periodic_row, s);
+    else
+        launch_fill_ghosts_ax<P, 0>(f, mask, chunks, row_nb, nchunks, bnodes, nbnodes, stride, n_row, periodic_row, s);
     return cudaGetLastError();
 }
 
@@ -1328,7 +1467,8 @@ cudaError_t launch_init_eq(void *f, const int32_t *soa, int64_t n, int64_t strid
     template cudaError_t launch_reduce<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \
                                           cudaStream_t);                                                           \
     template cudaError_t launch_fill_ghosts<P>(void *, const uint32_t *, const int2 *, const int4 *, int32_t,      \
-                                               const int4 *, int32_t, int64_t, int32_t, int32_t, cudaStream_t);    \
+                                               const int4 *, int32_t, int64_t, int32_t, int32_t, int32_t,          \
+                                               cudaStream_t);                                                      \
     template cudaError_t launch_moments<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \
                                            cudaStream_t);                                                          \
     template cudaError_t launch_get_populations<P>(const void *, const int32_t *, int64_t, int64_t, float,         \

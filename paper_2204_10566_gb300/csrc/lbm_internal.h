@@ -71,11 +71,14 @@ enum : uint32_t {
     CHUNK_LANES_SHIFT = 20,
 };
 
-// Row records: rows are indexed over the box extended by one ghost layer in
-// y and z, row = (y + 1) + (ny + 2) (z + 1).  Each row record holds the
-// storage bases of the nine neighbour rows (y - cy, z - cz), j = (cy + 1) +
-// 3 (cz + 1), so that the slot of the pull source of population i of cell x
-// is nb[j] + x - cx for every link (j = 4 is the row itself).
+// Row records: rows run along the row axis (x, or z for lattices longer in z
+// than in x).  In storage coordinates p (along the row) and a, b (across it),
+// (p, a, b) = (x, y, z) for rows along x and (z, x, y) for rows along z, and
+// rows are indexed over the box extended by one ghost layer in a and b,
+// row = (a + 1) + (n_a + 2) (b + 1).  Each row record holds the storage
+// bases of the nine neighbour rows (a - ca, b - cb), j = (ca + 1) + 3 (cb + 1),
+// so that the slot of the pull source of population i of the cell at p is
+// nb[j] + p - cp for every link (j = 4 is the row itself).
 constexpr int ROW_RECORD_INTS = 12;
 
 // Flow parameters in the arithmetic precision of a kernel.
@@ -97,10 +100,13 @@ struct alignas(16) StepArgs {
     int32_t nbnodes;
     int32_t fluid_blocks;   // blocks of the fluid kernel (offset of the boundary kernel's partials)
     uint32_t *status;       // bit 1: a bounded device wait gave up
-    int32_t nx, ny, nz, ny_e;
+    int32_t nx, ny, nz;     // box (physical x, y, z)
+    int32_t na_e;           // extended extent of the first cross axis (decodes a row index)
+    int32_t n_row;          // cells along the row axis
+    int32_t row_axis;       // 0: rows along x, 2: rows along z
     int32_t flags;          // STEP_REDUCE | STEP_STATS
     int32_t profile;
-    int32_t periodic_x;
+    int32_t periodic_row;   // the row axis is periodic (wrap-around copies at p = -1 and n_row)
     FlowParams<double> pd;
     FlowParams<float> pf;
     uint64_t seed;
@@ -139,8 +145,8 @@ cudaError_t launch_reduce(const void *f, const int32_t *slot_of_active, int64_t 
 // its active cells (after any host-side change of the state).
 template <int P>
 cudaError_t launch_fill_ghosts(void *f, const uint32_t *mask, const int2 *chunks, const int4 *row_nb,
-                               int32_t nchunks, const int4 *bnodes, int32_t nbnodes, int64_t stride, int32_t nx,
-                               int32_t periodic_x, cudaStream_t s);
+                               int32_t nchunks, const int4 *bnodes, int32_t nbnodes, int64_t stride, int32_t n_row,
+                               int32_t periodic_row, int32_t row_axis, cudaStream_t s);
 template <int P>
 cudaError_t launch_moments(const void *f, const int32_t *slot_of_active, int64_t n, int64_t stride,
                            float inv_scale, double *out4, cudaStream_t s);
@@ -167,7 +173,9 @@ struct HostIndex {
     int64_t n_active = 0;
     int64_t nslots = 0;
     int64_t n_ghost = 0;                  // bounce-back ghost slots
-    int32_t ny_e = 0, nz_e = 0;           // extended row grid
+    int32_t row_axis = 0;                 // 0: rows along x, 2: rows along z
+    int32_t n_row = 0;                    // cells along the row axis
+    int32_t na_e = 0, nb_e = 0;           // extended extents of the two cross axes (row grid)
     std::vector<int32_t> row_nb;          // [rows][ROW_RECORD_INTS]
     std::vector<int2> chunks;             // chunk records (fluid cells)
     std::vector<int4> bnodes;             // inlet/outlet nodes: x, row, slot, link word
@@ -183,9 +191,12 @@ constexpr int64_t MASK_MARGIN = 64;
 
 // Returns "" on success, else a description of the inconsistency.  With
 // max_slots > 0, a lattice needing more storage slots is refused before its
-// per-slot arrays are allocated.
+// per-slot arrays are allocated.  row_axis: LBM_ROWS_AUTO / X / Z.
 std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int periodic, HostIndex &out,
-                        int64_t max_slots = 0);
+                        int64_t max_slots = 0, int row_axis = LBM_ROWS_AUTO);
+// Row axis (0: x, 2: z) of a box for a requested LBM_ROWS_* value: AUTO takes
+// z when the box is longer in z than in x.
+int choose_row_axis(int nx, int ny, int nz, int requested);
 // Independent check of the index invariants the kernels rely on ("" if all hold).
 std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, int ny, int nz, int periodic);
 

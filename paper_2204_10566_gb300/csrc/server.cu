@@ -108,7 +108,12 @@ __global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_multi_flu
         if (!load_domain(e, k, sa)) continue;  // uniform over the block
         const int chunk = (tile - e.tile_begin) * (STEP_THREADS / CHUNK) + threadIdx.x / CHUNK;
         hv[5] = 0.0;
-        if (chunk < sa.nchunks) fluid_cell<P, true, false>(sa, chunk, threadIdx.x % CHUNK, hv);
+        if (chunk < sa.nchunks) {
+            if (sa.row_axis == 2)  // uniform over the block
+                fluid_cell<P, true, false, 2>(sa, chunk, threadIdx.x % CHUNK, hv);
+            else
+                fluid_cell<P, true, false, 0>(sa, chunk, threadIdx.x % CHUNK, hv);
+        }
         flag_non_finite(sa, hv);
     }
 }
@@ -127,7 +132,12 @@ __global__ void __launch_bounds__(STEP_THREADS) k_multi_boundary(const GroupTabl
         if (!load_domain(e, k, sa)) continue;
         const int node = (tile - e.btile_begin) * STEP_THREADS + threadIdx.x;
         hv[5] = 0.0;
-        if (node < sa.nbnodes) boundary_node<P, true, false>(sa, node, hv);
+        if (node < sa.nbnodes) {
+            if (sa.row_axis == 2)
+                boundary_node<P, true, false, 2>(sa, node, hv);
+            else
+                boundary_node<P, true, false, 0>(sa, node, hv);
+        }
         flag_non_finite(sa, hv);
     }
 }

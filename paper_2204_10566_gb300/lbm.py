@@ -23,6 +23,8 @@ LBM_SOLID, LBM_FLUID, LBM_INLET, LBM_OUTLET = 0, 1, 2, 3
 LBM_PROFILE_PLUG, LBM_PROFILE_PARABOLIC = 0, 1
 LBM_LAYOUT_ACTIVE, LBM_LAYOUT_BOX = 0, 1
 LBM_PERIODIC_X, LBM_PERIODIC_Y, LBM_PERIODIC_Z = 1, 2, 4
+LBM_ROWS_AUTO, LBM_ROWS_X, LBM_ROWS_Z = 0, 1, 2
+ROW_AXES = {"auto": LBM_ROWS_AUTO, "x": LBM_ROWS_X, "z": LBM_ROWS_Z}
 LBM_STATS_AXIAL, LBM_STATS_FULL = 0, 1
 LBM_STATS_FULL_COMPONENTS = 16
 
@@ -41,7 +43,7 @@ class lbm_desc(C.Structure):
     _fields_ = [
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
         ("periodic", C.c_int32), ("precision", C.c_int32),
-        ("fp16_scale", C.c_float), ("device", C.c_int32),
+        ("fp16_scale", C.c_float), ("device", C.c_int32), ("row_axis", C.c_int32),
         ("stream", C.c_void_p),
         ("allocator", lbm_allocator),
     ]
@@ -102,7 +104,7 @@ _SIGS = {
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_make_nozzle": (C.c_int, [C.c_int32] * 6 + [C.c_double, C.c_void_p]),
-    "lbm_check_layout": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+    "lbm_check_layout": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                    C.POINTER(C.c_int64)]),
     "lbm_set_geometry": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_fluid_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
@@ -241,17 +243,21 @@ def make_nozzle(D, d, L_total, L_in=None, L_cone=-1, L_throat=None, half_angle_d
     return out
 
 
-def check_layout(flags, periodic=0):
-    """lbm_check_layout: host-only index build + invariant check.  Returns a
-    dict of counts; raises LbmError on an inconsistent field or index."""
+def check_layout(flags, periodic=0, row_axis="auto"):
+    """lbm_check_layout: host-only index build + invariant check, rows along
+    row_axis ("auto", "x" or "z").  Returns a dict of counts (row_axis is the
+    axis used, "x" or "z"); raises LbmError on an inconsistent field or
+    index."""
     flags = np.ascontiguousarray(flags, dtype=np.uint8)
     nz, ny, nx = flags.shape
     out = (C.c_int64 * 8)()
-    st = capi().lbm_check_layout(flags.ctypes.data, nx, ny, nz, int(periodic), out)
+    st = capi().lbm_check_layout(flags.ctypes.data, nx, ny, nz, int(periodic), ROW_AXES[row_axis], out)
     if st != LBM_OK:
         raise LbmError(st, "lbm_check_layout")
-    keys = ["active", "slots", "segments", "chunks", "boundary_nodes", "wall_links", "rows"]
-    return dict(zip(keys, list(out)[:7]))
+    keys = ["active", "slots", "row_records", "chunks", "boundary_nodes", "wall_links", "rows"]
+    info = dict(zip(keys, list(out)[:7]))
+    info["row_axis"] = "z" if out[7] == LBM_ROWS_Z else "x"
+    return info
 
 
 class TorchAllocator:
@@ -290,7 +296,7 @@ class Lattice:
     """
 
     def __init__(self, flags, precision="fp32", periodic=0, fp16_scale=0.0, device=0, stream=None,
-                 torch_allocator=True, allocator=None):
+                 torch_allocator=True, allocator=None, row_axis="auto"):
         import torch
 
         self.lib = capi()
@@ -312,6 +318,7 @@ class Lattice:
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         d.fp16_scale = float(fp16_scale)
         d.device = device
+        d.row_axis = ROW_AXES[row_axis]
         d.stream = C.c_void_p(self.stream.cuda_stream)
         if self.allocator is not None:
             d.allocator = self.allocator.struct()

@@ -23,9 +23,9 @@ def oracle_lattice(orc, flags, nu, periodic=0, ghost=(1.0, 1.0, 1.0, 1.0), profi
 
 
 def gpu_lattice(lbm, flags, precision, nu, periodic=0, ghost=(1.0, 1.0, 1.0, 1.0), profile="plug", u_in=0.0,
-                d_in=None, noise_amp=0.0, seed=0, rho_out=1.0, fp16_scale=0.0, ramp=0):
+                d_in=None, noise_amp=0.0, seed=0, rho_out=1.0, fp16_scale=0.0, ramp=0, rows="auto"):
     nz, ny, nx = flags.shape
-    G = lbm.Lattice(flags, precision, periodic=periodic, fp16_scale=fp16_scale)
+    G = lbm.Lattice(flags, precision, periodic=periodic, fp16_scale=fp16_scale, row_axis=rows)
     G.set_params(nu=nu, ghost=ghost, u_in=u_in, d_in=d_in if d_in else nx, profile=profile,
                  noise_amp=noise_amp, noise_seed=seed, rho_out=rho_out, inlet_ramp=ramp)
     return G

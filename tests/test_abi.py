@@ -94,9 +94,10 @@ def _duct(n, nz, nx=None):
     return f
 
 
+@pytest.mark.parametrize("rows", ["x", "z"])
 @pytest.mark.parametrize("case", ["nozzle", "ragged", "box13", "box70", "duct", "pipe", "long_rows"])
-@pytest.mark.parametrize("periodic", [0, 7, 3])
-def test_layout_invariants(lib, case, periodic):
+@pytest.mark.parametrize("periodic", [0, 7, 3, 4])
+def test_layout_invariants(lib, case, periodic, rows):
     """The sparse index the kernels use: every staged copy aligned and in
     bounds, every fluid cell in exactly one work unit, every pull stored
     (checked on the host, independently of how the index was built)."""
@@ -119,10 +120,26 @@ def test_layout_invariants(lib, case, periodic):
         pytest.skip("walls of the nozzle need no periodic faces")
     if case == "duct" and periodic & 4:
         pytest.skip("inlet/outlet planes need a non-periodic z")
-    info = lbm.check_layout(f, periodic)
+    info = lbm.check_layout(f, periodic, rows)
     assert info["active"] == int((f != 0).sum())
     assert info["boundary_nodes"] == int(((f == 2) | (f == 3)).sum())
-    assert info["segments"] >= 1 and info["slots"] % 64 == 0
+    assert info["row_records"] >= 1 and info["slots"] % 64 == 0 and info["row_axis"] == rows
+
+
+def test_row_axis_choice(lib):
+    """AUTO stores rows along z when the box is longer in z than in x.  On the
+    Re 3500 nozzle that leaves far fewer chunk lanes idle than rows along x."""
+    f = I.workload_flags("nozzle_re3500_96x96x800")
+    assert lbm.check_layout(np.ones((4, 4, 9), dtype=np.uint8))["row_axis"] == "x"
+    assert lbm.check_layout(np.ones((9, 4, 4), dtype=np.uint8))["row_axis"] == "z"
+    assert lbm.check_layout(np.ones((9, 4, 9), dtype=np.uint8))["row_axis"] == "x"
+    auto = lbm.check_layout(f)
+    xr = lbm.check_layout(f, 0, "x")
+    assert auto["row_axis"] == "z"
+    assert auto["active"] == xr["active"] == 4286996
+    idle_z = 1.0 - auto["active"] / (8.0 * auto["chunks"])
+    idle_x = 1.0 - xr["active"] / (8.0 * xr["chunks"])
+    assert idle_z < 0.5 * idle_x, (idle_z, idle_x)
 
 
 def test_layout_rejects_inconsistent_fields(lib):

@@ -31,11 +31,11 @@ def lbm():
 
 
 def run_both(orc, lbm, flags, precision, steps, nu=0.02, periodic=0, seed=0, ghost=(1.0, 1.0, 1.0, 1.0),
-             **bc):
+             rows="auto", **bc):
     O = oracle_lattice(orc, flags, nu, periodic=periodic, ghost=ghost, **bc)
     f0 = random_state(orc, flags, seed)
     O.set_populations(f0)
-    G = gpu_lattice(lbm, flags, precision, nu, periodic=periodic, ghost=ghost, **bc)
+    G = gpu_lattice(lbm, flags, precision, nu, periodic=periodic, ghost=ghost, rows=rows, **bc)
     G.set_populations(f0, layout=BOX)
     O.step(steps)
     G.step(steps).sync()
@@ -56,18 +56,20 @@ def ragged_flags():
     return f
 
 
+@pytest.mark.parametrize("rows", ["x", "z"])
 @pytest.mark.parametrize("ghost", [(1.0, 1.0, 1.0, 1.0), (0.8, 1.2, 1.5, 0.6)])
-def test_periodic_fp64_elementwise(orc, lbm, ghost):
+def test_periodic_fp64_elementwise(orc, lbm, ghost, rows):
     flags = np.ones((5, 6, 13), dtype=np.uint8)
-    O, G, act = run_both(orc, lbm, flags, "fp64", 3, periodic=7, ghost=ghost)
+    O, G, act = run_both(orc, lbm, flags, "fp64", 3, periodic=7, ghost=ghost, rows=rows)
     fg = G.get_populations(BOX)
     assert max_rel(fg[act], O.f[act]) < 1e-13
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
-def test_walls_ragged_rows(orc, lbm, precision, tol):
+@pytest.mark.parametrize("rows", ["x", "z"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6), ("fp16s", 3e-3)])
+def test_walls_ragged_rows(orc, lbm, precision, tol, rows):
     flags = ragged_flags()
-    O, G, act = run_both(orc, lbm, flags, precision, 4, nu=0.05)
+    O, G, act = run_both(orc, lbm, flags, precision, 4, nu=0.05, rows=rows)
     fg = G.get_populations(BOX)
     assert max_rel(fg[act], O.f[act]) < tol
     rho, u = G.moments(BOX)
@@ -77,8 +79,9 @@ def test_walls_ragged_rows(orc, lbm, precision, tol):
         assert np.abs(u[act] - mo[act, 1:]).max() < 1e-14
 
 
+@pytest.mark.parametrize("rows", ["x", "z"])
 @pytest.mark.parametrize("precision,ramp", [("fp64", 0), ("fp32", 0), ("fp16s", 0), ("fp64", 4), ("fp32", 4)])
-def test_nee_duct_parabolic_noise(orc, lbm, precision, ramp):
+def test_nee_duct_parabolic_noise(orc, lbm, precision, ramp, rows):
     """Velocity inlet (parabolic profile + seeded noise, impulsive or ramped
     start) and pressure outlet by non-equilibrium extrapolation, periodic
     cross-section."""
@@ -86,7 +89,7 @@ def test_nee_duct_parabolic_noise(orc, lbm, precision, ramp):
     flags[0] = 2
     flags[-1] = 3
     bc = dict(profile="parabolic", u_in=0.03, d_in=8.0, noise_amp=0.02, seed=77, rho_out=1.001, ramp=ramp)
-    O, G, act = run_both(orc, lbm, flags, precision, 6, nu=0.03, periodic=3, **bc)
+    O, G, act = run_both(orc, lbm, flags, precision, 6, nu=0.03, periodic=3, rows=rows, **bc)
     fg = G.get_populations(BOX)
     rho, u = G.moments(BOX)
     mo = O.moments()
@@ -97,7 +100,8 @@ def test_nee_duct_parabolic_noise(orc, lbm, precision, ramp):
         assert rel_l2(u[act], mo[act, 1:]) < tol
 
 
-def test_noise_draws_bit_exact(orc, lbm):
+@pytest.mark.parametrize("rows", ["x", "z"])
+def test_noise_draws_bit_exact(orc, lbm, rows):
     """The inlet perturbation is integer work: the boundary velocity the GPU
     imposes equals the oracle's prescribed value to FP64 rounding at every
     inlet node, for several steps (a single wrong bit of the hash would
@@ -106,7 +110,7 @@ def test_noise_draws_bit_exact(orc, lbm):
     flags[0] = 2
     flags[-1] = 3
     bc = dict(profile="plug", u_in=0.02, noise_amp=0.5, seed=123456789)
-    O, G, act = run_both(orc, lbm, flags, "fp64", 3, nu=0.05, periodic=3, **bc)
+    O, G, act = run_both(orc, lbm, flags, "fp64", 3, nu=0.05, periodic=3, rows=rows, **bc)
     rho, u = G.moments(BOX)
     inlet = flags.reshape(-1) == 2
     assert np.abs(u[inlet] - O.moments()[inlet, 1:]).max() < 1e-15
@@ -129,11 +133,12 @@ def re500_oracle(orc):
     return flags, O
 
 
+@pytest.mark.parametrize("rows", ["x", "z"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
-def test_nozzle_re500_100_steps(lbm, re500_oracle, precision):
+def test_nozzle_re500_100_steps(lbm, re500_oracle, precision, rows):
     flags, O = re500_oracle
     _, nu, bc = nozzle_re500_setup()
-    G = gpu_lattice(lbm, flags, precision, nu, **bc)
+    G = gpu_lattice(lbm, flags, precision, nu, rows=rows, **bc)
     G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
     G.step(100).sync()
     act = flags.reshape(-1) != 0

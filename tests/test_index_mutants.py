@@ -22,30 +22,33 @@ CSRC = os.path.join(ROOT, "paper_2204_10566_gb300", "csrc")
 # name: (text in geometry.cpp, planted text)
 MUTANTS = {
     "ghost_marks_wrong_array": (
-        "out.mask[(size_t)(base[row_of(ys, zs)] + x - cx)] |= 1u << i;",
-        "out.mask[(size_t)(base[row_of(ys, zs)] + x - cx)] |= 1u << (26 - i);"),
-    "neighbour_row_direction": ("int yy = y - cy, zz = z - cz;", "int yy = y + cy, zz = z - cz;"),
-    "neighbour_rows_y_z_swapped": (
-        "out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(yy, zz)];",
-        "out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(zz % ny, yy % nz)];"),
+        "out.mask[(size_t)(base[row_of(as, bs)] + p - cp)] |= 1u << i;",
+        "out.mask[(size_t)(base[row_of(as, bs)] + p - cp)] |= 1u << (26 - i);"),
+    "neighbour_row_direction": ("int aa = a - ca, bb = b - cb;", "int aa = a + ca, bb = b - cb;"),
+    "neighbour_rows_cross_axes_swapped": (
+        "out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(aa, bb)];",
+        "out.row_nb[(size_t)r * ROW_RECORD_INTS + j] = base[row_of(bb % F.na, aa % F.nb)];"),
     "boundary_nodes_in_chunk_lanes": (
-        "if (x < nx && flags[box_index(x, y, z, nx, ny)] == LBM_FLUID) lanes |= 1u << l;",
-        "if (x < nx && flags[box_index(x, y, z, nx, ny)] != LBM_SOLID) lanes |= 1u << l;"),
+        "if (p < F.np && flags[F.box(p, a, b)] == LBM_FLUID) lanes |= 1u << l;",
+        "if (p < F.np && flags[F.box(p, a, b)] != LBM_SOLID) lanes |= 1u << l;"),
     "row_range_one_short": (
         "const int hi = ((need_hi[r] + 1 + CHUNK - 1) / CHUNK) * CHUNK;",
         "const int hi = ((need_hi[r] + CHUNK - 1) / CHUNK) * CHUNK;"),
     "periodic_copy_wrong_arrays": (
-        "for (int i = 2; i < 27; i += 3) out.mask[(size_t)(base[r] - 1)] |= 1u << i;",
-        "for (int i = 0; i < 27; i += 3) out.mask[(size_t)(base[r] - 1)] |= 1u << i;"),
+        "if (F.pp && p == F.np - 1 && cp == 1) out.mask[(size_t)(base[r] - 1)] |= 1u << i;",
+        "if (F.pp && p == F.np - 1 && cp == -1) out.mask[(size_t)(base[r] - 1)] |= 1u << i;"),
     "boundary_node_slot": (
-        "out.bnodes.push_back(make_int4(x, (int)row_of(y, z), slot, (int)out.mask[(size_t)slot]));",
-        "out.bnodes.push_back(make_int4(x, (int)row_of(y, z), slot + 1, (int)out.mask[(size_t)slot]));"),
-    "active_slot_shifted": ("const int32_t slot = base[row_of(y, z)] + x;", "const int32_t slot = base[row_of(y, z)] + x + 1;"),
-    "ghost_row_not_wrapped": ("        ys = py ? yw : y;", "        ys = y;"),
-    "neighbour_row_not_wrapped": ("                if (py) yy = (yy + ny) % ny;\n", ""),
+        "out.bnodes.push_back(make_int4(p, (int)row_of(a, b), slot, (int)out.mask[(size_t)slot]));",
+        "out.bnodes.push_back(make_int4(p, (int)row_of(a, b), slot + 1, (int)out.mask[(size_t)slot]));"),
+    "active_slot_shifted": ("const int32_t slot = base[row_of(a, b)] + p;", "const int32_t slot = base[row_of(a, b)] + p + 1;"),
+    "ghost_row_not_wrapped": ("        as = F.pa ? aw : a;", "        as = a;"),
+    "neighbour_row_not_wrapped": ("                if (F.pa) aa = (aa + F.na) % F.na;\n", ""),
     "chunk_start_unaligned": (
-        "for (int x0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; x0 <= act_hi[r]; x0 += CHUNK) {",
-        "for (int x0 = act_lo[r]; x0 <= act_hi[r]; x0 += CHUNK) {"),
+        "for (int p0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; p0 <= act_hi[r]; p0 += CHUNK) {",
+        "for (int p0 = act_lo[r]; p0 <= act_hi[r]; p0 += CHUNK) {"),
+    "z_rows_cross_directions_swapped": ("            cp = cz, ca = cx, cb = cy;", "            cp = cz, ca = cy, cb = cx;"),
+    "z_rows_storage_order": ("        return ax == 0 ? box_index(p, a, b, nx, ny) : box_index(a, b, p, nx, ny);",
+                             "        return ax == 0 ? box_index(p, a, b, nx, ny) : box_index(b, a, p, nx, ny);"),
 }
 
 # the flag fields each case is checked on: (name, shape, recipe, periodic)
@@ -70,18 +73,20 @@ def side_inlet():
     return f
 
 cases = [(I.workload_flags("nozzle_re500_24x24x160"), 0), (ragged(), 0), (ragged(), 7), (ragged(), 3),
-         (np.ones((5, 6, 13), dtype=np.uint8), 7), (duct(), 0), (duct(), 3), (I.pipe_flags(18, 30), 0),
-         (side_inlet(), 0)]
+         (ragged(), 5), (np.ones((5, 6, 13), dtype=np.uint8), 7), (np.ones((13, 6, 5), dtype=np.uint8), 7),
+         (duct(), 0), (duct(), 3), (I.pipe_flags(18, 30), 0), (side_inlet(), 0)]
 L = C.CDLL(LIB)
-L.lbm_check_layout.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
+L.lbm_check_layout.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                               C.POINTER(C.c_int64)]
 refused = 0
 for f, p in cases:
     f = np.ascontiguousarray(f, dtype=np.uint8)
     nz, ny, nx = f.shape
-    out = (C.c_int64 * 8)()
-    st = L.lbm_check_layout(f.ctypes.data, nx, ny, nz, p, out)
-    ok = st == 0 and out[0] == int((f != 0).sum()) and out[4] == int(((f == 2) | (f == 3)).sum())
-    refused += not ok
+    for rows in (1, 2):  # rows along x, rows along z
+        out = (C.c_int64 * 8)()
+        st = L.lbm_check_layout(f.ctypes.data, nx, ny, nz, p, rows, out)
+        ok = st == 0 and out[0] == int((f != 0).sum()) and out[4] == int(((f == 2) | (f == 3)).sum())
+        refused += not ok
 print(refused)
 '''
 
