@@ -37,14 +37,18 @@ struct lbm_ctx {
     int4 *d_wnodes = nullptr;        // cells with interpolated walls, out of the chunk lanes
     int64_t n_wnodes = 0;
     int2 *d_chunks_wall = nullptr;   // chunk records without those cells (the fluid kernel's list)
+    int32_t *d_tiles_wall = nullptr; // tile records without those cells
+    int64_t n_tiles_wall = 0;
     bool wide_offsets = false;       // LBM_WIDE_OFFSETS=1 at creation: the 64-bit offset kernels always
+    bool chunk_kernel = false;       // LBM_FLUID_KERNEL=chunk at creation: no staged fluid kernel
+    int32_t *d_tiles = nullptr;      // tile records of the staged fluid kernel
+    int staged_blocks = 0;           // grid of the staged fluid kernel (0: not available)
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
     double *d_stats = nullptr;
     int nblocks = 0;        // partial-sum capacity (blocks)
-    int step_blocks = 0;    // blocks of one step (fluid + boundary kernels)
-    int fluid_blocks = 0;   // blocks of the fluid kernel
+    int fluid_blocks = 0;   // blocks of the chunk fluid kernel
     int64_t device_bytes = 0;
     // parameters and state
     lbm_params params{};
@@ -124,7 +128,10 @@ void release_wall_q(lbm_ctx *c) {
     dev_free(c, c->d_wall_q, (size_t)c->n_wall_q * 32);
     dev_free(c, c->d_wnodes, (size_t)c->n_wnodes * 16);
     if (c->d_chunks_wall) dev_free(c, c->d_chunks_wall, c->idx.chunks.size() * 8);
+    if (c->d_tiles_wall) dev_free(c, c->d_tiles_wall, (size_t)c->n_tiles_wall * TILE_INTS * 4);
     c->d_chunks_wall = nullptr;
+    c->d_tiles_wall = nullptr;
+    c->n_tiles_wall = 0;
     c->d_wall_qidx = nullptr;
     c->d_wall_q = nullptr;
     c->d_wnodes = nullptr;
@@ -141,6 +148,8 @@ void release_geometry(lbm_ctx *c) {
     dev_free(c, c->d_chunks, c->idx.chunks.size() * 8);
     dev_free(c, c->d_bnodes, c->idx.bnodes.size() * 16);
     dev_free(c, c->d_slot_of_active, c->idx.slot_of_active.size() * 4);
+    dev_free(c, c->d_tiles, c->idx.tiles.size() * 4);
+    c->d_tiles = nullptr;
     release_wall_q(c);
     dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     dev_free(c, c->d_health, 8 * 8);
@@ -194,6 +203,32 @@ int periodic_rows(const lbm_ctx *c) {
     return (c->desc.periodic & (c->idx.row_axis == 2 ? LBM_PERIODIC_Z : LBM_PERIODIC_X)) ? 1 : 0;
 }
 
+// Whether the next steps run the staged fluid kernel (FP32 / FP16S, default
+// ghost rates, 32-bit offsets), and the partial sums the step kernels write:
+// the fluid kernel's blocks, then the inlet/outlet blocks, then the wall-cell
+// blocks.
+bool wide_offsets(const lbm_ctx *c) { return c->wide_offsets || c->idx.nslots > MAX_SLOTS_32; }
+int64_t tile_count(const lbm_ctx *c) {
+    return c->d_tiles_wall ? c->n_tiles_wall : (int64_t)c->idx.tiles.size() / TILE_INTS;
+}
+bool staged(const lbm_ctx *c) {
+    return c->desc.precision != LBM_FP64 && c->ghost1 && !wide_offsets(c) && !c->chunk_kernel &&
+           c->staged_blocks > 0 && tile_count(c) > 0;
+}
+// Grid of the staged kernel: the blocks resident at once, fewer for a small lattice (4 warps a block).
+int staged_grid_now(const lbm_ctx *c) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(c->staged_blocks, (tile_count(c) + 3) / 4));
+}
+int fluid_partials(const lbm_ctx *c) { return staged(c) ? staged_grid_now(c) : c->fluid_blocks; }
+int step_partials(const lbm_ctx *c) {
+    return fluid_partials(c) + node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(c->n_wnodes);
+}
+// Partial-sum capacity for either fluid kernel, the wall cells and lbm_get_totals.
+int partial_capacity(const lbm_ctx *c, int64_t n_wnodes) {
+    const int nodes = node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(n_wnodes);
+    return std::max({c->fluid_blocks + nodes, c->staged_blocks + nodes, node_blocks(c->idx.n_active)});
+}
+
 // Ghost slots and periodic copies of the current buffer from its active cells.
 cudaError_t fill_ghosts(lbm_ctx *c) {
     return DISPATCH(c->desc.precision, launch_fill_ghosts, c->f[c->cur], c->d_mask, c->d_chunks, c->d_row_nb,
@@ -227,7 +262,7 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.nchunks = (int32_t)c->idx.chunks.size();
     a.bnodes = c->d_bnodes;
     a.nbnodes = (int32_t)c->idx.bnodes.size();
-    a.fluid_blocks = c->fluid_blocks;
+    a.fluid_blocks = fluid_partials(c);
     a.status = c->d_status;
     a.nx = c->desc.nx;
     a.ny = c->desc.ny;
@@ -261,7 +296,12 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.stats = c->d_stats;
     a.partials = c->d_partials;
     a.wide_offsets = c->wide_offsets ? 1 : 0;
-    const bool wide = a.wide_offsets || a.stride > MAX_SLOTS_32;
+    const bool wide = wide_offsets(c);
+    if (staged(c)) {
+        a.tiles = c->d_tiles_wall ? c->d_tiles_wall : c->d_tiles;
+        a.ntiles = (int32_t)tile_count(c);
+        a.staged_blocks = staged_grid_now(c);
+    }
     const int key = (c->ghost1 ? 2 : 0) + (wide ? 1 : 0);
     if (c->prefetch_key != key) {
         c->prefetch_ahead = DISPATCH(c->desc.precision, step_prefetch_ahead, c->ghost1, wide, c->desc.device);
@@ -354,6 +394,10 @@ lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out) {
     // without allocating tens of gigabytes.
     const char *wide = std::getenv("LBM_WIDE_OFFSETS");
     c->wide_offsets = wide && wide[0] == '1';
+    // LBM_FLUID_KERNEL=chunk runs the chunk fluid kernel where the staged one
+    // would run (for testing both on the same lattices)
+    const char *fk = std::getenv("LBM_FLUID_KERNEL");
+    c->chunk_kernel = fk && std::strcmp(fk, "chunk") == 0;
     lbm_params_default(&c->params);
     *out = c;
     return LBM_OK;
@@ -378,7 +422,6 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     DeviceGuard g(c->desc.device);
     CK(cudaStreamSynchronize(c->stream), "sync before wall distances");
     release_wall_q(c);
-    c->step_blocks = c->fluid_blocks + node_blocks((int64_t)c->idx.bnodes.size());  // no wall kernel
     if (n == 0) return LBM_OK;
     const int64_t ncell = (int64_t)c->desc.nx * c->desc.ny * c->desc.nz;
     // box index -> active index, to find each cell's slot
@@ -429,23 +472,29 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
             if (((lanes >> l) & 1u) && is_wall[(size_t)(base + x0 + l)]) lanes &= ~(1u << l);
         ch.y = (int)((uint32_t)x0 | (lanes << CHUNK_LANES_SHIFT));
     }
+    const std::vector<int32_t> tiles = wn.empty() ? std::vector<int32_t>() : build_tiles(chunks, c->idx.row_nb);
     c->d_wall_qidx = (int32_t *)dev_alloc(c, qidx.size() * 4);
     c->d_wall_q = (uint8_t *)dev_alloc(c, rec.size());
     c->n_wall_q = n;
     c->n_wnodes = (int64_t)wn.size();
     c->d_wnodes = wn.empty() ? nullptr : (int4 *)dev_alloc(c, wn.size() * 16);
     if (!wn.empty()) c->d_chunks_wall = (int2 *)dev_alloc(c, chunks.size() * 8);
-    const int step_blocks = c->fluid_blocks + node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(c->n_wnodes);
+    if (!wn.empty()) {
+        c->n_tiles_wall = (int64_t)tiles.size() / TILE_INTS;
+        c->d_tiles_wall = (int32_t *)dev_alloc(c, tiles.size() * 4);
+    }
+    const int capacity = partial_capacity(c, c->n_wnodes);
     double *partials = c->d_partials;
-    if (step_blocks > c->nblocks) {  // room for the wall kernel's partial sums
-        partials = (double *)dev_alloc(c, (size_t)step_blocks * REDUCE_SLOTS * 8);
+    if (capacity > c->nblocks) {  // room for the wall kernel's partial sums
+        partials = (double *)dev_alloc(c, (size_t)capacity * REDUCE_SLOTS * 8);
         if (partials) {
             dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
             c->d_partials = partials;
-            c->nblocks = step_blocks;
+            c->nblocks = capacity;
         }
     }
-    if (!c->d_wall_qidx || !c->d_wall_q || (!wn.empty() && (!c->d_wnodes || !c->d_chunks_wall)) || !partials) {
+    if (!c->d_wall_qidx || !c->d_wall_q || (!wn.empty() && (!c->d_wnodes || !c->d_chunks_wall || !c->d_tiles_wall)) ||
+        !partials) {
         release_wall_q(c);
         return fail(c, LBM_ERR_OOM, "wall-distance allocation failed");
     }
@@ -458,7 +507,9 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     if (!wn.empty())
         CK(cudaMemcpyAsync(c->d_chunks_wall, chunks.data(), chunks.size() * 8, cudaMemcpyHostToDevice, c->stream),
            "copy chunk lanes");
-    c->step_blocks = step_blocks;
+    if (!tiles.empty())
+        CK(cudaMemcpyAsync(c->d_tiles_wall, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, c->stream),
+           "copy tile records");
     CK(cudaStreamSynchronize(c->stream), "sync wall distances");
     return LBM_OK;
 }
@@ -484,7 +535,8 @@ int64_t ctx_footprint(const lbm_desc &d, const HostIndex &ix) {
     const int64_t blocks = std::max<int64_t>(fluid_blocks((int32_t)ix.chunks.size()) + node_blocks((int64_t)ix.bnodes.size()),
                                              node_blocks(ix.n_active));
     return 2 * pop + (ix.nslots + 2 * MASK_MARGIN) * 4 + (int64_t)ix.row_nb.size() * 4 + (int64_t)ix.chunks.size() * 8 +
-           (int64_t)ix.bnodes.size() * 16 + ix.n_active * 4 + blocks * REDUCE_SLOTS * 8 + 64 + 256;
+           (int64_t)ix.bnodes.size() * 16 + ix.n_active * 4 + (int64_t)ix.tiles.size() * 4 +
+           blocks * REDUCE_SLOTS * 8 + 64 + 256;
 }
 
 lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
@@ -494,8 +546,11 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
     c->idx = std::move(idx);
     const size_t ns = (size_t)c->idx.nslots;
     c->fluid_blocks = DISPATCH(c->desc.precision, step_fluid_blocks, (int32_t)c->idx.chunks.size());
-    c->step_blocks = c->fluid_blocks + node_blocks((int64_t)c->idx.bnodes.size());
-    c->nblocks = std::max(c->step_blocks, node_blocks(c->idx.n_active));
+    c->staged_blocks = c->desc.precision == LBM_FP64
+                           ? 0
+                           : (c->desc.precision == LBM_FP32 ? staged_grid<1>(c->desc.device, c->idx.row_axis)
+                                                            : staged_grid<2>(c->desc.device, c->idx.row_axis));
+    c->nblocks = partial_capacity(c, 0);
     for (int k = 0; k < 2; ++k) {
         c->f_raw[k] = dev_alloc(c, raw_pop_bytes(c));
         c->f[k] = c->f_raw[k] ? static_cast<char *>(c->f_raw[k]) + margin_bytes(c) : nullptr;
@@ -506,11 +561,12 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
     c->d_chunks = (int2 *)dev_alloc(c, c->idx.chunks.size() * 8);
     c->d_bnodes = (int4 *)dev_alloc(c, c->idx.bnodes.size() * 16);
     c->d_slot_of_active = (int32_t *)dev_alloc(c, c->idx.slot_of_active.size() * 4);
+    c->d_tiles = (int32_t *)dev_alloc(c, c->idx.tiles.size() * 4);
     c->d_partials = (double *)dev_alloc(c, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     c->d_health = (double *)dev_alloc(c, 8 * 8);
     c->d_status = (uint32_t *)dev_alloc(c, 256);
     if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_nb || !c->d_chunks || !c->d_bnodes || !c->d_slot_of_active ||
-        !c->d_partials || !c->d_health || !c->d_status) {
+        !c->d_tiles || !c->d_partials || !c->d_health || !c->d_status) {
         release_geometry(c);
         return fail(c, LBM_ERR_OOM, "device allocation failed in lbm_set_geometry");
     }
@@ -529,6 +585,10 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
     CK(cudaMemcpyAsync(c->d_slot_of_active, c->idx.slot_of_active.data(), c->idx.slot_of_active.size() * 4,
                        cudaMemcpyHostToDevice, c->stream),
        "copy slot map");
+    if (!c->idx.tiles.empty())
+        CK(cudaMemcpyAsync(c->d_tiles, c->idx.tiles.data(), c->idx.tiles.size() * 4, cudaMemcpyHostToDevice,
+                           c->stream),
+           "copy tile records");
     // Padding slots are never read by the step kernel; zero both buffers so
     // that checkpoints and dumps are deterministic.
     CK(cudaMemsetAsync(c->f_raw[0], 0, raw_pop_bytes(c), c->stream), "clear f0");
@@ -771,7 +831,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
             ++c->stats_samples;
         }
         CK(DISPATCH(c->desc.precision, launch_step, a, c->ghost1, c->stream), "step kernel");
-        if (check) CK(launch_finalize(c->d_partials, c->step_blocks, c->d_health, c->d_status, c->stream), "finalize");
+        if (check) CK(launch_finalize(c->d_partials, step_partials(c), c->d_health, c->d_status, c->stream), "finalize");
         c->cur = 1 - c->cur;
         c->t = t_new;
     }

@@ -268,7 +268,37 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
             }
         }
     if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
+    out.tiles = build_tiles(out.chunks, out.row_nb);
     return "";
+}
+
+std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb) {
+    std::vector<int32_t> tiles;
+    int row = -1, p0 = 0, n = 0;  // the open tile
+    uint32_t fluid = 0, present = 0;
+    auto flush = [&]() {
+        if (n == 0) return;
+        tiles.push_back(p0);
+        tiles.push_back((int32_t)fluid);
+        tiles.push_back((int32_t)present);
+        for (int j = 0; j < 9; ++j) tiles.push_back(row_nb[(size_t)row * ROW_RECORD_INTS + j]);
+        n = 0;
+    };
+    for (const int2 &c : chunks) {
+        const int x0 = (int)((uint32_t)c.y & CHUNK_X0_MASK);
+        const uint32_t lanes = ((uint32_t)c.y >> CHUNK_LANES_SHIFT) & 0xFFu;
+        if (n == 0 || n == 4 || c.x != row || x0 != p0 + CHUNK * n) {
+            flush();
+            row = c.x;
+            p0 = x0;
+            fluid = present = 0;
+        }
+        fluid |= lanes << (CHUNK * n);
+        present |= 0xFFu << (CHUNK * n);
+        ++n;
+    }
+    flush();
+    return tiles;
 }
 
 // Structural invariants of an index, re-derived independently of how
@@ -397,6 +427,43 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     }
     for (const int4 &n : ix.bnodes)
         if (n.z < 0 || n.z >= ns || ix.row_nb[(size_t)n.y * ROW_RECORD_INTS + 4] + n.x != n.z) return "boundary node";
+
+    // Tiles of the staged kernel: every fluid cell in exactly one fluid lane,
+    // at its own slot, with the bases of its own row; every window a tile
+    // stages (pulls from p0 - 8 .. p0 + 39 of each neighbour row, link words
+    // of p0 .. p0 + 31) inside the buffer and its margins.
+    const int64_t nt = (int64_t)ix.tiles.size() / TILE_INTS;
+    if ((int64_t)ix.tiles.size() != nt * TILE_INTS) return "tile record size";
+    std::vector<int64_t> box_of_slot((size_t)ns, -1);
+    for (int64_t k = 0; k < ix.n_active; ++k) box_of_slot[(size_t)ix.slot_of_active[k]] = ix.box_of_active[k];
+    std::vector<uint8_t> in_tile((size_t)nx * ny * nz, 0);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int32_t *rec = &ix.tiles[(size_t)t * TILE_INTS];
+        const int p0 = rec[0];
+        const uint32_t fl = (uint32_t)rec[1], pr = (uint32_t)rec[2];
+        const int32_t *tb = rec + 3;
+        if (p0 % CHUNK || (fl & ~pr)) return "tile start or lanes";
+        for (int j = 0; j < 9; ++j) {
+            const int64_t lo = (int64_t)tb[j] + p0 - 8, hi = (int64_t)tb[j] + p0 + 40;
+            if (lo < -margin || hi > ns + margin) return "tile window outside the buffer";
+        }
+        if ((int64_t)tb[4] + p0 < 0 || (int64_t)tb[4] + p0 + 32 > ns + MASK_MARGIN) return "tile link words";
+        for (int l = 0; l < 32; ++l) {
+            if (!((pr >> l) & 1u)) continue;
+            const int64_t s = (int64_t)tb[4] + p0 + l;
+            if (s < 0 || s >= ns) return "tile lane outside the buffer";
+            if (!((fl >> l) & 1u)) continue;
+            const int64_t bx = box_of_slot[(size_t)s];
+            if (bx < 0 || flags[bx] != LBM_FLUID || in_tile[(size_t)bx]++) return "tile lane is not a unique fluid cell";
+            int p, a, b;
+            pab_of(bx, p, a, b);
+            if (p != p0 + l) return "tile lane position";
+            for (int j = 0; j < 9; ++j)
+                if (ix.row_nb[(size_t)row_e(a, b) * ROW_RECORD_INTS + j] != tb[j]) return "tile bases";
+        }
+    }
+    for (int64_t b = 0; b < (int64_t)in_tile.size(); ++b)
+        if ((flags[b] == LBM_FLUID) != (in_tile[b] == 1)) return "fluid cell not in exactly one tile lane";
 
     return "";
 }
