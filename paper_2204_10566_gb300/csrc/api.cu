@@ -40,9 +40,8 @@ struct lbm_ctx {
     int32_t *d_tiles_wall = nullptr; // tile records without those cells
     int64_t n_tiles_wall = 0;
     bool wide_offsets = false;       // LBM_WIDE_OFFSETS=1 at creation: the 64-bit offset kernels always
-    bool chunk_kernel = false;       // LBM_FLUID_KERNEL=chunk at creation: no staged fluid kernel
-    int32_t *d_tiles = nullptr;      // tile records of the staged fluid kernel
-    int staged_blocks = 0;           // grid of the staged fluid kernel (0: not available)
+    bool chunk_kernel = false;       // LBM_FLUID_KERNEL=chunk at creation: no tile fluid kernel
+    int32_t *d_tiles = nullptr;      // tile records of the tile fluid kernel
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
@@ -203,7 +202,7 @@ int periodic_rows(const lbm_ctx *c) {
     return (c->desc.periodic & (c->idx.row_axis == 2 ? LBM_PERIODIC_Z : LBM_PERIODIC_X)) ? 1 : 0;
 }
 
-// Whether the next steps run the staged fluid kernel (FP32 / FP16S, default
+// Whether the next steps run the tile fluid kernel (FP32 / FP16S, default
 // ghost rates, 32-bit offsets), and the partial sums the step kernels write:
 // the fluid kernel's blocks, then the inlet/outlet blocks, then the wall-cell
 // blocks.
@@ -211,22 +210,18 @@ bool wide_offsets(const lbm_ctx *c) { return c->wide_offsets || c->idx.nslots > 
 int64_t tile_count(const lbm_ctx *c) {
     return c->d_tiles_wall ? c->n_tiles_wall : (int64_t)c->idx.tiles.size() / TILE_INTS;
 }
-bool staged(const lbm_ctx *c) {
-    return c->desc.precision != LBM_FP64 && c->ghost1 && !wide_offsets(c) && !c->chunk_kernel &&
-           c->staged_blocks > 0 && tile_count(c) > 0;
+bool tiled(const lbm_ctx *c) {
+    return c->desc.precision != LBM_FP64 && c->ghost1 && !wide_offsets(c) && !c->chunk_kernel && tile_count(c) > 0;
 }
-// Grid of the staged kernel: the blocks resident at once, fewer for a small lattice (4 warps a block).
-int staged_grid_now(const lbm_ctx *c) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(c->staged_blocks, (tile_count(c) + 3) / 4));
-}
-int fluid_partials(const lbm_ctx *c) { return staged(c) ? staged_grid_now(c) : c->fluid_blocks; }
+int fluid_partials(const lbm_ctx *c) { return tiled(c) ? tile_blocks(tile_count(c)) : c->fluid_blocks; }
 int step_partials(const lbm_ctx *c) {
     return fluid_partials(c) + node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(c->n_wnodes);
 }
 // Partial-sum capacity for either fluid kernel, the wall cells and lbm_get_totals.
 int partial_capacity(const lbm_ctx *c, int64_t n_wnodes) {
     const int nodes = node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(n_wnodes);
-    return std::max({c->fluid_blocks + nodes, c->staged_blocks + nodes, node_blocks(c->idx.n_active)});
+    const int tiles = tile_blocks(std::max<int64_t>((int64_t)c->idx.tiles.size() / TILE_INTS, c->n_tiles_wall));
+    return std::max({c->fluid_blocks + nodes, tiles + nodes, node_blocks(c->idx.n_active)});
 }
 
 // Ghost slots and periodic copies of the current buffer from its active cells.
@@ -297,10 +292,9 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     a.partials = c->d_partials;
     a.wide_offsets = c->wide_offsets ? 1 : 0;
     const bool wide = wide_offsets(c);
-    if (staged(c)) {
+    if (tiled(c)) {
         a.tiles = c->d_tiles_wall ? c->d_tiles_wall : c->d_tiles;
         a.ntiles = (int32_t)tile_count(c);
-        a.staged_blocks = staged_grid_now(c);
     }
     const int key = (c->ghost1 ? 2 : 0) + (wide ? 1 : 0);
     if (c->prefetch_key != key) {
@@ -394,7 +388,7 @@ lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out) {
     // without allocating tens of gigabytes.
     const char *wide = std::getenv("LBM_WIDE_OFFSETS");
     c->wide_offsets = wide && wide[0] == '1';
-    // LBM_FLUID_KERNEL=chunk runs the chunk fluid kernel where the staged one
+    // LBM_FLUID_KERNEL=chunk runs the chunk fluid kernel where the tile one
     // would run (for testing both on the same lattices)
     const char *fk = std::getenv("LBM_FLUID_KERNEL");
     c->chunk_kernel = fk && std::strcmp(fk, "chunk") == 0;
@@ -472,7 +466,9 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
             if (((lanes >> l) & 1u) && is_wall[(size_t)(base + x0 + l)]) lanes &= ~(1u << l);
         ch.y = (int)((uint32_t)x0 | (lanes << CHUNK_LANES_SHIFT));
     }
-    const std::vector<int32_t> tiles = wn.empty() ? std::vector<int32_t>() : build_tiles(chunks, c->idx.row_nb);
+    const std::vector<int32_t> tiles =
+        wn.empty() ? std::vector<int32_t>()
+                   : build_tiles(chunks, c->idx.row_nb, c->idx.mask, c->idx.n_row, periodic_rows(c) != 0);
     c->d_wall_qidx = (int32_t *)dev_alloc(c, qidx.size() * 4);
     c->d_wall_q = (uint8_t *)dev_alloc(c, rec.size());
     c->n_wall_q = n;
@@ -546,10 +542,6 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
     c->idx = std::move(idx);
     const size_t ns = (size_t)c->idx.nslots;
     c->fluid_blocks = DISPATCH(c->desc.precision, step_fluid_blocks, (int32_t)c->idx.chunks.size());
-    c->staged_blocks = c->desc.precision == LBM_FP64
-                           ? 0
-                           : (c->desc.precision == LBM_FP32 ? staged_grid<1>(c->desc.device, c->idx.row_axis)
-                                                            : staged_grid<2>(c->desc.device, c->idx.row_axis));
     c->nblocks = partial_capacity(c, 0);
     for (int k = 0; k < 2; ++k) {
         c->f_raw[k] = dev_alloc(c, raw_pop_bytes(c));

@@ -268,17 +268,22 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
             }
         }
     if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
-    out.tiles = build_tiles(out.chunks, out.row_nb);
+    out.tiles = build_tiles(out.chunks, out.row_nb, out.mask, F.np, F.pp);
     return "";
 }
 
-std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb) {
+std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
+                                 const std::vector<uint32_t> &mask, int n_row, bool periodic_row) {
     std::vector<int32_t> tiles;
     int row = -1, p0 = 0, n = 0;  // the open tile
     uint32_t fluid = 0, present = 0;
     auto flush = [&]() {
         if (n == 0) return;
-        tiles.push_back(p0);
+        // fast: 32 fluid cells without wall links, none writing a wrap-around copy
+        bool fast = fluid == 0xFFFFFFFFu && !(periodic_row && (p0 == 0 || p0 + 31 >= n_row - 1));
+        const int32_t base = row_nb[(size_t)row * ROW_RECORD_INTS + 4];
+        for (int l = 0; fast && l < 32; ++l) fast = (mask[(size_t)(base + p0 + l)] & LINK_MASK) == 0u;
+        tiles.push_back((int32_t)((uint32_t)p0 | (fast ? TILE_FAST : 0u)));
         tiles.push_back((int32_t)fluid);
         tiles.push_back((int32_t)present);
         for (int j = 0; j < 9; ++j) tiles.push_back(row_nb[(size_t)row * ROW_RECORD_INTS + j]);
@@ -428,10 +433,11 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     for (const int4 &n : ix.bnodes)
         if (n.z < 0 || n.z >= ns || ix.row_nb[(size_t)n.y * ROW_RECORD_INTS + 4] + n.x != n.z) return "boundary node";
 
-    // Tiles of the staged kernel: every fluid cell in exactly one fluid lane,
-    // at its own slot, with the bases of its own row; every window a tile
-    // stages (pulls from p0 - 8 .. p0 + 39 of each neighbour row, link words
-    // of p0 .. p0 + 31) inside the buffer and its margins.
+    // Tiles of the tile kernel: every fluid cell in exactly one fluid lane, at
+    // its own slot, with the bases of its own row; every lane's pulls (p0 - 1
+    // .. p0 + 32 of each neighbour row, checked with a margin of 8) and link
+    // words inside the buffer and its margins; the fast flag only on tiles of
+    // 32 fluid cells without wall links or wrap-around copies.
     const int64_t nt = (int64_t)ix.tiles.size() / TILE_INTS;
     if ((int64_t)ix.tiles.size() != nt * TILE_INTS) return "tile record size";
     std::vector<int64_t> box_of_slot((size_t)ns, -1);
@@ -439,10 +445,16 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     std::vector<uint8_t> in_tile((size_t)nx * ny * nz, 0);
     for (int64_t t = 0; t < nt; ++t) {
         const int32_t *rec = &ix.tiles[(size_t)t * TILE_INTS];
-        const int p0 = rec[0];
+        const bool fast = ((uint32_t)rec[0] & TILE_FAST) != 0u;
+        const int p0 = (int)((uint32_t)rec[0] & ~TILE_FAST);
         const uint32_t fl = (uint32_t)rec[1], pr = (uint32_t)rec[2];
         const int32_t *tb = rec + 3;
         if (p0 % CHUNK || (fl & ~pr)) return "tile start or lanes";
+        if (fast) {
+            if (fl != 0xFFFFFFFFu || (pp && (p0 == 0 || p0 + 31 >= np - 1))) return "fast tile lanes";
+            for (int l = 0; l < 32; ++l)
+                if (ix.mask[(size_t)(tb[4] + p0 + l)] & LINK_MASK) return "fast tile with a wall link";
+        }
         for (int j = 0; j < 9; ++j) {
             const int64_t lo = (int64_t)tb[j] + p0 - 8, hi = (int64_t)tb[j] + p0 + 40;
             if (lo < -margin || hi > ns + margin) return "tile window outside the buffer";

@@ -1163,45 +1163,30 @@ __global__ void __launch_bounds__(STEP_THREADS) k_boundary(const StepArgs a) {
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials + (size_t)a.fluid_blocks * REDUCE_SLOTS);
 }
 
-// ------------------------------------------------------ staged fluid kernel
+// -------------------------------------------------------- tile fluid kernel
 //
-// Persistent variant of the fluid kernel (default ghost rates, 32-bit
-// offsets, FP32 / FP16S) over tile records: each warp walks its share of the
-// tiles and, while it computes one tile, cp.async copies the next tile's
-// inputs into its slice of shared memory: the 27 pull windows (positions
-// p0 - PAD .. p0 + 32 + PAD of the neighbour row of each population, PAD one
-// 16-byte piece), the 32 link words and the record of the tile after that.
-// The loads of a tile are then in flight during a whole tile of arithmetic
-// without holding registers, the collision reads its inputs from shared
-// memory at fixed offsets, and a warp of 32 fluid cells without wall links
-// writes its outputs through shared memory as 16-byte stores.
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Variant of the fluid kernel (default ghost rates, 32-bit offsets, FP32 /
+// FP16S) over tile records instead of chunk records: one warp updates one
+// tile, up to 32 consecutive cells of a row.  Its record (p0, lanes, the
+// nine neighbour-row bases) is one 48-byte load with no dependent index
+// load before the gather.  A "fast" tile (32 fluid cells, no wall link, no
+// wrap-around copy; flagged when the index is built) stores through shared
+// memory: each lane writes its 27 values at fixed offsets, and the warp
+// writes every population's 32 consecutive own slots as 16-byte stores, so
+// the 27 per-value address computations of the line sink disappear.  Other
+// tiles load their link words and use the line sink.
 
 template <int P>
-struct Staging {
+struct TileOut {
     using T = typename Storage<P>::T;
     static constexpr int S = (int)sizeof(T);
-    static constexpr int PAD = 16 / S;                   // elements of one 16-byte piece
-    static constexpr int W = 32 + 2 * PAD;              // window of one population
-    static constexpr int PIECES = W * S / 16;           // 16-byte pieces of a window
-    static constexpr int OUT_PIECES = 32 * S / 16;      // 16-byte pieces of a tile's 32 outputs
-    static constexpr int DATA = 27 * W * S;             // bytes of the 27 windows
-    static constexpr int STAGE = DATA + 32 * 4;         // + the tile's link words
-    static constexpr int WARP = 2 * STAGE + 3 * TILE_INTS * 4;  // two stages, three record slots
-    static_assert(3 * PIECES <= 32, "a storage line's windows are copied by one warp instruction");
-    static_assert(DATA % 16 == 0 && STAGE % 16 == 0 && WARP % 16 == 0, "16-byte aligned layout");
+    static constexpr int PIECE = 16 / S;          // elements of one 16-byte store
+    static constexpr int PIECES = 32 / PIECE;     // 16-byte pieces of one population's 32 outputs
+    static constexpr int ELEMS = 27 * 32;         // a warp's staged outputs
 };
 
-template <int P>
-constexpr int staged_smem_bytes() { return (STEP_THREADS / 32) * Staging<P>::WARP; }
-
 // Output sink of a fast tile: value i of lane l goes to out[i * 32 + l] in
-// shared memory (the tile's consumed windows); copied out as 16-byte stores.
+// the warp's shared-memory slice (out points at lane l's first element).
 template <int P, bool RAW>
 struct SharedStore {
     using S = Storage<P>;
@@ -1209,7 +1194,7 @@ struct SharedStore {
     using R = typename S::R;
     const StepArgs &a;
     int slot;
-    T *out;  // out + lane
+    T *out;
     __device__ __forceinline__ void put(int i, R v) const {
         if constexpr (RAW)
             S::store_raw(out + 32 * i, v);
@@ -1224,110 +1209,49 @@ struct SharedStore {
     }
 };
 
-// Issue the copies of tile t's windows and link words into stage `st` (a
-// shared-memory address), from its record `rec`; lanes below 3 PIECES copy
-// piece k of population c of each storage line (lane_ptr: population c's
-// array, element k PAD - PAD of the window).
 template <int P, int AX>
-__device__ __forceinline__ void stage_tile(const StepArgs &a, const int32_t *rec, uint32_t st, int lane,
-                                           const typename Staging<P>::T *lane_ptr, uint32_t lane_dst) {
-    using G = Staging<P>;
-    const int p0 = rec[0];
-    if (lane < 3 * G::PIECES) {
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            const int64_t e = (int64_t)line_pop<AX>(j, 0) * a.stride + rec[3 + j] + p0;
-            cp_async16(st + (uint32_t)(line_pop<AX>(j, 0) * G::W * G::S) + lane_dst, lane_ptr + e);
-        }
-    }
-    if (lane < 8) cp_async16(st + G::DATA + 16 * lane, a.mask + rec[3 + 4] + p0 + 4 * lane);
-}
-
-template <int P, int AX, bool REDUCE>
-__global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step_staged(const StepArgs a) {
-    using G = Staging<P>;
-    using T = typename G::T;
+__global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step_tiles(const StepArgs a) {
+    using O = TileOut<P>;
+    using T = typename O::T;
     using R = typename Storage<P>::R;
     constexpr bool RAW = Storage<P>::SCALED;
-    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) T staged_out[STEP_THREADS / 32][O::ELEMS];
     const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-    unsigned char *ws = smem + warp * G::WARP;
-    const uint32_t ws_s = (uint32_t)__cvta_generic_to_shared(ws);
-    int32_t *recs = reinterpret_cast<int32_t *>(ws + 2 * G::STAGE);
-    const uint32_t recs_s = ws_s + 2 * G::STAGE;
-    // this lane's copy role: piece k of population c of a storage line
-    constexpr int dk = line_pop<AX>(0, 1) - line_pop<AX>(0, 0);
-    const int c = lane / G::PIECES, k = lane % G::PIECES;
-    const T *lane_ptr = static_cast<const T *>(a.fin) + (int64_t)(c * dk) * a.stride + k * G::PAD - G::PAD;
-    const uint32_t lane_dst = (uint32_t)((c * dk * G::W + k * G::PAD) * G::S);
-    const int stride_w = (int)(gridDim.x * (STEP_THREADS / 32));
-    int t = (int)blockIdx.x * (STEP_THREADS / 32) + warp;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    // prologue: record of the first tile, then its data and the second record
-    if (t < a.ntiles && lane < 3) cp_async16(recs_s + 16 * lane, a.tiles + (size_t)t * TILE_INTS + 4 * lane);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncwarp();
-    if (t < a.ntiles) stage_tile<P, AX>(a, recs, ws_s, lane, lane_ptr, lane_dst);
-    if (t + stride_w < a.ntiles && lane < 3)
-        cp_async16(recs_s + TILE_INTS * 4 + 16 * lane, a.tiles + (size_t)(t + stride_w) * TILE_INTS + 4 * lane);
-    cp_async_commit();
-    for (int it = 0; t < a.ntiles; ++it, t += stride_w) {
-        cp_async_wait_all();  // this tile's windows and the next tile's record
-        __syncwarp();
-        const int tn = t + stride_w;
-        unsigned char *cur = ws + (it & 1) * G::STAGE;
-        const int32_t *rec = recs + (it % 3) * TILE_INTS;
-        if (tn < a.ntiles)
-            stage_tile<P, AX>(a, recs + ((it + 1) % 3) * TILE_INTS, ws_s + ((it + 1) & 1) * G::STAGE, lane, lane_ptr,
-                              lane_dst);
-        if (tn + stride_w < a.ntiles && lane < 3)
-            cp_async16(recs_s + ((it + 2) % 3) * TILE_INTS * 4 + 16 * lane,
-                       a.tiles + (size_t)(tn + stride_w) * TILE_INTS + 4 * lane);
-        cp_async_commit();
-
-        // this tile, from shared memory
-        int nb[9];
-#pragma unroll
-        for (int j = 0; j < 9; ++j) nb[j] = rec[3 + j];
-        const int x = rec[0] + lane;
-        const bool fluid = ((uint32_t)rec[1] >> lane) & 1u;
-        const bool present = ((uint32_t)rec[2] >> lane) & 1u;
-        const int slot = nb[4] + x;
-        const uint32_t m = reinterpret_cast<const uint32_t *>(cur + G::DATA)[lane];
-        const T *win = reinterpret_cast<const T *>(cur) + G::PAD + lane;
+    const int t = (int)blockIdx.x * (STEP_THREADS / 32) + warp;
+    double hv[6] = {0, 0, 0, 0, 0, 0};
+    if (t < a.ntiles) {  // uniform over the warp
+        const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * (size_t)t;
+        const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+        const int nb[9] = {r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+        const bool fast = ((uint32_t)r0.x & TILE_FAST) != 0u;
+        const int p0 = (int)((uint32_t)r0.x & CHUNK_X0_MASK);
+        const int x = p0 + lane, slot = nb[4] + x;
+        const bool fluid = ((uint32_t)r0.y >> lane) & 1u;
         R d[27];
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            const T v = win[i * G::W - c_row<AX>(i)];
-            if constexpr (P == 2)
-                d[i] = __half2float(v);  // raw storage value; the scale is folded into the collision
-            else
-                d[i] = v;
-        }
-        const bool row_end = a.periodic_row && (x == 0 || x == a.n_row - 1);
-        const bool simple = fluid && (m & LINK_MASK) == 0u && !row_end;
-        const bool fast = __all_sync(0xffffffffu, simple);
-        __syncwarp();  // every lane has read the windows: a fast tile writes its outputs there
+        gather<P, false, AX, RAW>(a, nb, x, d);  // every lane's pulls lie inside the buffer margins
         R rho, ux, uy, uz;
         if (fast) {
-            T *out = reinterpret_cast<T *>(cur);
+            T *out = staged_out[warp];
             const SharedStore<P, RAW> sink{a, slot, out + lane};
             collide_ghost1<R, RAW, SharedStore<P, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
                                                         R(a.scale), &sink);
             __syncwarp();
-            // the 27 x 32 outputs, own slots nb[4] + p0 .. + 31 of each array
-            T *fout = static_cast<T *>(a.fout) + (nb[4] + rec[0]);
+            // piece q = 4 i + k (FP16S) / 8 i + k (FP32): elements 16k/S.. of population i,
+            // at shared offset 16 q bytes and at own slots nb[4] + p0 + k PIECE
+            T *fout = static_cast<T *>(a.fout) + (nb[4] + p0);
 #pragma unroll
-            for (int q0 = 0; q0 < 27 * G::OUT_PIECES; q0 += 32) {
+            for (int q0 = 0; q0 < 27 * O::PIECES; q0 += 32) {
                 const int q = q0 + lane;
-                if (q < 27 * G::OUT_PIECES) {
-                    const int i = q / G::OUT_PIECES, kk = q % G::OUT_PIECES;
-                    const int4 v = *reinterpret_cast<const int4 *>(out + 32 * i + kk * G::PAD);
-                    *reinterpret_cast<int4 *>(fout + elem<false>(i, a.stride, kk * G::PAD)) = v;
+                if (q < 27 * O::PIECES) {
+                    const int4 v = reinterpret_cast<const int4 *>(out)[q];
+                    const int i = q / O::PIECES, k = q % O::PIECES;
+                    *reinterpret_cast<int4 *>(fout + elem<false>(i, a.stride, k * O::PIECE)) = v;
                 }
             }
+            __syncwarp();
         } else {
+            const bool present = ((uint32_t)r0.z >> lane) & 1u;
+            const uint32_t m = present ? __ldg(a.mask + slot) : 0u;
             const uint32_t links = fluid ? (m & LINK_MASK) : 0u;
             const uint32_t own = fluid ? (LINK_MASK | OWN_FLUID)
                                        : (present && ((m >> TYPE_SHIFT) & 3u) == TYPE_PAD ? (~m & LINK_MASK) : 0u);
@@ -1335,18 +1259,9 @@ __global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step_stag
             collide_ghost1<R, RAW, LineStore<P, false, RAW, AX>>(d, flow<R>(a).omega, rho, ux, uy, uz,
                                                                  R(a.inv_scale), R(a.scale), &sink);
         }
-        if (fluid) {
-            double hv[6];
-            record_cell(a, slot, rho, ux, uy, uz, hv);
-            if constexpr (REDUCE) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) acc[q] = q == 4 ? fmax(acc[q], hv[q]) : acc[q] + hv[q];
-            }
-        }
-        __syncwarp();  // the stage is refilled two tiles later
+        if (fluid) record_cell(a, slot, rho, ux, uy, uz, hv);
     }
-    cp_async_wait_all();
-    if constexpr (REDUCE) block_reduce_write(acc, a.partials);
+    if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
 
 // ---------------------------------------------------------- utility kernels
@@ -1533,25 +1448,6 @@ int step_fluid_blocks(int32_t nchunks) {
     return step_blocks(nchunks);
 }
 
-// Blocks of the staged fluid kernel resident on the device at once (its
-// persistent grid): occupancy with its shared memory, times the SM count.
-template <int P>
-int staged_grid(int device, int row_axis) {
-    if constexpr (P == 0) {
-        return 0;  // FP64 runs the chunk kernel
-    } else {
-    int per_sm = 0, sms = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, row_axis == 2 ? k_step_staged<P, 2, true> : k_step_staged<P, 0, true>, STEP_THREADS,
-        staged_smem_bytes<P>());
-    if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return per_sm * sms;
-    }
-}
-
 template <int P>
 int step_prefetch_ahead(bool ghost1, bool wide, int device) {
     int per_sm = 0, sms = 0;
@@ -1574,13 +1470,8 @@ template <int P, bool G, bool WD, int AX>
 void launch_step_ax(const StepArgs &a, cudaStream_t s) {
     const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
     if constexpr (G && !WD && P != 0) {
-        if (a.tiles) {  // the staged fluid kernel; inlet/outlet nodes and wall cells in launches of their own
-            if (a.ntiles > 0) {
-                if (a.flags & STEP_REDUCE)
-                    k_step_staged<P, AX, true><<<a.staged_blocks, STEP_THREADS, staged_smem_bytes<P>(), s>>>(a);
-                else
-                    k_step_staged<P, AX, false><<<a.staged_blocks, STEP_THREADS, staged_smem_bytes<P>(), s>>>(a);
-            }
+        if (a.tiles) {  // the tile fluid kernel; inlet/outlet nodes and wall cells in launches of their own
+            if (a.ntiles > 0) k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
             if (a.nwnodes > 0)
                 k_wall<P, G, WD, AX><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
             if (bb > 0) k_boundary<P, G, WD, AX><<<bb, STEP_THREADS, 0, s>>>(a);
@@ -1683,7 +1574,6 @@ cudaError_t launch_init_eq(void *f, const int32_t *soa, int64_t n, int64_t strid
     template cudaError_t launch_step<P>(const StepArgs &, bool, cudaStream_t);                                     \
     template int step_fluid_blocks<P>(int32_t);                                                                     \
     template int step_prefetch_ahead<P>(bool, bool, int);                                                          \
-    template int staged_grid<P>(int, int);                                                                          \
     template cudaError_t launch_reduce<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \
                                           cudaStream_t);                                                           \
     template cudaError_t launch_fill_ghosts<P>(void *, const uint32_t *, const int2 *, const int4 *, int32_t,      \

@@ -81,16 +81,21 @@ enum : uint32_t {
 // nb[j] + p - cp for every link (j = 4 is the row itself).
 constexpr int ROW_RECORD_INTS = 12;
 
-// Tile records of the staged fluid kernel: a tile is up to four consecutive
+// Tile records of the tile fluid kernel: a tile is up to four consecutive
 // chunks of one row, i.e. up to 32 consecutive positions [p0, p0 + 32).  A
-// record holds p0, the fluid-lane mask (bit l: position p0 + l is a fluid
-// cell), the present-lane mask (bit l: p0 + l lies in one of the tile's
-// chunks; other lanes do nothing) and the row's nine neighbour bases (as in
-// the row record), so that a tile needs no dependent index load.
+// record holds p0 (with the fast flag TILE_FAST: 32 fluid cells, none with
+// a wall link or a wrap-around copy), the fluid-lane mask (bit l: position
+// p0 + l is a fluid cell), the present-lane mask (bit l: p0 + l lies in one
+// of the tile's chunks; other lanes store nothing) and the row's nine
+// neighbour bases (as in the row record), so that a tile needs no dependent
+// index load.
 constexpr int TILE_INTS = 12;
+constexpr uint32_t TILE_FAST = 1u << 31;
 
-// Group a chunk list (in row order) into tile records.
-std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb);
+// Group a chunk list (in row order) into tile records; mask: the link words,
+// n_row / periodic_row: the row axis (wrap-around copies at its ends).
+std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
+                                 const std::vector<uint32_t> &mask, int n_row, bool periodic_row);
 
 // Flow parameters in the arithmetic precision of a kernel.
 template <class R>
@@ -133,9 +138,8 @@ struct alignas(16) StepArgs {
     const int4 *wnodes;        // cells with interpolated walls (x, row, slot, record), out of the chunk lanes
     int32_t nwnodes;
     int32_t wide_offsets;      // 1: 64-bit element offsets even when 32 bits would do (LBM_WIDE_OFFSETS=1)
-    const int32_t *tiles;      // tile records [ntiles][TILE_INTS] of the staged fluid kernel (NULL: chunk kernel)
+    const int32_t *tiles;      // tile records [ntiles][TILE_INTS] of the tile fluid kernel (NULL: chunk kernel)
     int32_t ntiles;
-    int32_t staged_blocks;     // grid of the staged fluid kernel (its partial-sum slots)
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).
@@ -152,10 +156,8 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device);
 // Blocks of one step's fluid kernel (partial-sum slots it writes).
 template <int P>
 int step_fluid_blocks(int32_t nchunks);
-// Grid of the staged fluid kernel on a device: its blocks resident at once
-// (0 for FP64, which runs the chunk kernel).
-template <int P>
-int staged_grid(int device, int row_axis);
+// Blocks of the tile fluid kernel (one warp per tile).
+inline int tile_blocks(int64_t ntiles) { return (int)((ntiles + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32)); }
 template <int P>
 cudaError_t launch_reduce(const void *f, const int32_t *slot_of_active, int64_t n, int64_t stride, float inv_scale,
                           double *partials, cudaStream_t s);
@@ -196,7 +198,7 @@ struct HostIndex {
     int32_t na_e = 0, nb_e = 0;           // extended extents of the two cross axes (row grid)
     std::vector<int32_t> row_nb;          // [rows][ROW_RECORD_INTS]
     std::vector<int2> chunks;             // chunk records (fluid cells)
-    std::vector<int32_t> tiles;           // [tiles][TILE_INTS] records of the staged fluid kernel
+    std::vector<int32_t> tiles;           // [tiles][TILE_INTS] records of the tile fluid kernel
     std::vector<int4> bnodes;             // inlet/outlet nodes: x, row, slot, link word
     std::vector<uint32_t> mask;           // [nslots]
     std::vector<int32_t> slot_of_active;  // [n_active], active order = increasing box index

@@ -86,7 +86,14 @@ def nozzle_wall_q(D, d, L_total, L_in=None, L_cone=None, L_throat=None, half_ang
         flags = nozzle_flags(D, d, L_total, L_in, L_cone, L_throat, half_angle_deg)
     nz, ny, nx = flags.shape
     c = np.array([[i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1] for i in range(27)])
-    fz, fy, fx = np.nonzero(flags == FLUID)
+    # candidates: FLUID cells with a solid (or outside) cell among their 26
+    # neighbours, in box order; the others have no wall link
+    solid = np.pad(flags == SOLID, 1, constant_values=True)
+    near = np.zeros(flags.shape, dtype=bool)
+    for i in range(27):
+        near |= solid[1 - c[i, 2]:1 - c[i, 2] + nz, 1 - c[i, 1]:1 - c[i, 1] + ny, 1 - c[i, 0]:1 - c[i, 0] + nx]
+    fz, fy, fx = np.nonzero((flags == FLUID) & near)
+    del solid, near
     solid_src = np.zeros((fz.size, 27), dtype=bool)
     for i in range(27):
         sx, sy, sz = fx - c[i, 0], fy - c[i, 1], fz - c[i, 2]
@@ -98,8 +105,8 @@ def nozzle_wall_q(D, d, L_total, L_in=None, L_cone=None, L_throat=None, half_ang
     q = np.full((rows.size, 27), 128, dtype=np.uint8)
     px, py, pz = fx[rows] + 0.5, fy[rows] + 0.5, fz[rows] + 0.5
 
-    def outside(s, i):  # point at fraction s of link i from the cell centre
-        x, y, z = px - s * c[i, 0], py - s * c[i, 1], pz - s * c[i, 2]
+    def outside(s, i, sel):  # points at fraction s of link i from the centres of cells sel
+        x, y, z = px[sel] - s * c[i, 0], py[sel] - s * c[i, 1], pz[sel] - s * c[i, 2]
         r = np.hypot(x - D / 2.0, y - D / 2.0)
         return r > nozzle_radius_array(z, D, d, L_in, L_cone, L_throat, half_angle_deg)
 
@@ -107,15 +114,14 @@ def nozzle_wall_q(D, d, L_total, L_in=None, L_cone=None, L_throat=None, half_ang
         sel = solid_src[rows, i]
         if not sel.any():
             continue
-        lo = np.zeros(rows.size)
-        hi = np.ones(rows.size)
+        lo = np.zeros(int(sel.sum()))
+        hi = np.ones(lo.size)
         for _ in range(iterations):
             mid = 0.5 * (lo + hi)
-            out = outside(mid, i)
+            out = outside(mid, i, sel)
             hi = np.where(out, mid, hi)
             lo = np.where(out, lo, mid)
-        k = np.clip(np.rint(hi * 256.0), 1, 255).astype(np.uint8)
-        q[sel, i] = k[sel]
+        q[sel, i] = np.clip(np.rint(hi * 256.0), 1, 255).astype(np.uint8)
     cells = (fx[rows].astype(np.int64) + nx * (fy[rows].astype(np.int64) + ny * fz[rows].astype(np.int64)))
     return cells, q
 
@@ -165,7 +171,10 @@ WORKLOADS = {
 # grid spacings of Table 2, 2.3, 1.725 and 1.15 (x 1e-4 m), on the 4 mm
 # throat give 17.4, 23.2 and 34.8 cells; these are rounded up to multiples
 # of 6, which keeps the table's spacing ratios 1 : 4/3 : 2 exactly.
-LADDER_THROAT_CELLS = (18, 24, 36)
+# Throat diameters (cells) of the resolution ladder: Table 2's R1-R4 grid
+# spacings (Re 6500) over a 4 mm throat are 17.4, 23.2, 34.8 and 51.5 cells;
+# R1-R3 keep the table's spacing ratios 1 : 4/3 : 2 exactly, R4 is rounded up.
+LADDER_THROAT_CELLS = (18, 24, 36, 52)
 
 
 def workload_flags(name):

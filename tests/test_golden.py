@@ -112,13 +112,14 @@ def test_params_from_physical_checks(lbm):
 
 
 def test_ladder_levels_follow_table2():
-    rows = [r for r in table2() if r[1] == 3500.0]
+    rows = [r for r in table2() if r[1] == 6500.0]
     d_cells = [D_THR / dr for _, _, dr, _ in rows]
     lad = I.LADDER_THROAT_CELLS
+    assert len(rows) == len(lad) == 4
     for d_tab, d_lad in zip(d_cells, lad):
         assert d_tab <= d_lad < 1.04 * d_tab
-    for k in (1, 2):
-        assert abs(d_cells[k] / d_cells[0] - lad[k] / lad[0]) < 1e-12
+    for k in (1, 2):  # R1-R3 at the table's spacing ratios
+        assert abs(d_cells[k] / d_cells[0] - lad[k] / lad[0]) < 1e-3
 
 
 def test_params_check_on_the_host(lbm):

@@ -1,8 +1,11 @@
 """Flow-level checks of the CUDA path (GPU required): periodic Taylor-Green
 vortices against the oracle and the exact decay, and the time-averaged axial
-velocity of the transitional / turbulent nozzles across storage precisions
-(pointwise agreement is lost to chaos there; the averaged profiles must agree
-within 2 %)."""
+velocity of the transitional / turbulent nozzles across storage precisions.
+Pointwise agreement is lost to chaos there; the averaged radial profiles of
+FP32 and FP16S must agree with the FP64 GPU run within 2 % where the
+averages converge within the window (upstream of the sudden expansion and
+the jet's near field), and within the run-to-run variability further
+downstream."""
 import numpy as np
 import pytest
 
@@ -219,12 +222,30 @@ def test_square_duct_poiseuille_convergence(lbm):
     assert e8 / e16 > 3.0 and e16 / e32 > 3.0
 
 
-def nozzle_profile_run(lbm, name, precision, steps, avg_from):
-    """<u_z> time-averaged over steps avg_from+1 .. steps (FP64 accumulators):
-    centreline, eight cross-section planes, and the plane positions."""
+def radial_profiles(m1, flags):
+    """Azimuthal means of a box field m1 (nz, ny, nx) over the fluid cells of
+    each plane, in unit-width radial bins about the nozzle axis: (nz, bins)."""
+    nz, ny, nx = flags.shape
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    rb = np.floor(np.hypot(xx + 0.5 - nx / 2.0, yy + 0.5 - ny / 2.0)).astype(int).ravel()
+    nbins = rb.max() + 1
+    out = np.zeros((nz, nbins))
+    for z in range(nz):
+        w = (flags[z] != 0).ravel().astype(float)
+        cnt = np.bincount(rb, weights=w, minlength=nbins)
+        out[z] = np.bincount(rb, weights=w * m1[z].ravel(), minlength=nbins) / np.maximum(cnt, 1.0)
+    return out
+
+
+def nozzle_stats_run(lbm, name, precision, steps, avg_from, seed=None):
+    """<u_z> time-averaged over steps avg_from+1 .. steps (FP64 accumulators)
+    as radial profiles on every plane, and the sample count."""
     flags = I.workload_flags(name)
+    params = dict(I.workload_params(name))
+    if seed is not None:
+        params["noise_seed"] = seed
     G = lbm.Lattice(flags, precision)
-    G.set_params(**I.workload_params(name))
+    G.set_params(**params)
     G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
     G.step(avg_from)
     G.stats_begin(1)
@@ -232,10 +253,7 @@ def nozzle_profile_run(lbm, name, precision, steps, avg_from):
     m1, m2, n = G.stats_get(BOX)
     G.close()
     assert np.isfinite(m1).all() and np.isfinite(m2).all()
-    nz, ny, nx = flags.shape
-    m1 = m1.reshape(nz, ny, nx)
-    zs = np.linspace(0, nz - 1, 10).astype(int)[1:-1]
-    return m1[:, ny // 2, nx // 2], m1[zs], zs, n
+    return radial_profiles(m1.reshape(flags.shape), flags), n
 
 
 def expansion_start(name):
@@ -243,41 +261,60 @@ def expansion_start(name):
     return w["D"] + I.cone_length(w["D"], w["d"]) + 4 * w["d"]
 
 
-def check_statistics(name, ref, run, tol=0.02):
-    """Averages are compared where they are statistically converged within
-    the run: profiles up to the sudden expansion (inlet pipe, cone, throat),
-    where the jet has not yet broken down, and the plane-integrated axial
-    flux (fixed by mean mass conservation) on every plane.  Downstream of
-    the expansion the flow is chaotic and 10 000 steps are less than one
-    flow-through time, so pointwise averages differ between any two runs."""
-    rc, rp, zs, _ = ref
-    c, p, _, _ = run
-    z_exp = expansion_start(name)
-    assert rel_l2(c[:z_exp], rc[:z_exp]) < tol
-    up = zs < z_exp
-    assert rel_l2(p[up], rp[up]) < tol
-    flux_ref = rp.reshape(len(zs), -1).sum(1)
-    flux = p.reshape(len(zs), -1).sum(1)
-    assert np.max(np.abs(flux - flux_ref) / np.abs(flux_ref)) < tol
+def statistics_regions(name):
+    """Plane ranges of the statistics check: upstream of the sudden
+    expansion (inlet pipe, cone, throat), the near field of the jet (the first
+    two throat diameters after the expansion) and the far field (the rest,
+    short of the outlet planes)."""
+    w = I.WORKLOADS[name]
+    z_exp, d, nz = expansion_start(name), w["d"], w["L_total"]
+    return {"upstream": np.arange(4, z_exp), "near field": np.arange(z_exp, z_exp + 2 * d),
+            "far field": np.arange(z_exp + 2 * d, nz - 4)}
+
+
+def check_statistics(name, ref, runs, floor_run):
+    """Time-averaged axial velocity of each run in runs against the FP64 run
+    ref, as the relative L2 difference of the radial profiles over the planes
+    of each region: within 2 % upstream of the expansion and in the near field
+    of the jet, where the averages converge within the window; in the far
+    field, where the jet breaks down and two realizations differ by more than
+    2 % over any affordable window, within the run-to-run variability: 1.5
+    times the difference between ref and floor_run (the same flow with another
+    inlet-noise seed) plus 1 %."""
+    regions = statistics_regions(name)
+    rel = lambda a, b, zs: float(np.linalg.norm(a[zs] - b[zs]) / np.linalg.norm(b[zs]))
+    floor = rel(floor_run, ref, regions["far field"])
+    report = {"far-field noise floor": floor}
+    for label, prof in runs.items():
+        for region, zs in regions.items():
+            e = rel(prof, ref, zs)
+            report["%s %s" % (label, region)] = e
+            bound = 0.02 if region != "far field" else 1.5 * floor + 0.01
+            assert e < bound, (label, region, e, bound)
+    print(name, {k: round(v, 4) for k, v in report.items()})
+    return report
 
 
 def test_transitional_nozzle_time_averaged_profiles(lbm):
     """Re 3500 nozzle (96x96x800, parabolic inlet + 1 % noise), 20 000 steps
-    averaged over steps 10 001-20 000: FP32 and FP16-shifted <u_z> within 2 %
-    of the FP64 GPU run."""
+    averaged over steps 10 001-20 000: FP32 and FP16-shifted <u_z> against the
+    FP64 GPU run, region by region (check_statistics)."""
     name = "nozzle_re3500_96x96x800"
-    ref = nozzle_profile_run(lbm, name, "fp64", 20000, 10000)
-    assert ref[3] == 10000
-    for precision in ("fp32", "fp16s"):
-        check_statistics(name, ref, nozzle_profile_run(lbm, name, precision, 20000, 10000))
+    ref, n = nozzle_stats_run(lbm, name, "fp64", 20000, 10000)
+    assert n == 10000
+    floor = nozzle_stats_run(lbm, name, "fp32", 20000, 10000, seed=3)[0]
+    runs = {p: nozzle_stats_run(lbm, name, p, 20000, 10000)[0] for p in ("fp32", "fp16s")}
+    check_statistics(name, ref, runs, floor)
 
 
-def test_turbulent_nozzle_fp16s_vs_fp32(lbm):
-    """Re 6500 nozzle (144x144x1200, parabolic inlet + 2 % noise, smooth
-    start over 8000 steps): FP16-shifted storage against FP32, FP64
-    statistics accumulators, the full 50 000 steps averaged over the second
-    half: stays finite, <u_z> within 2 %."""
+def test_turbulent_nozzle_time_averaged_profiles(lbm):
+    """Re 6500 nozzle (144x144x1200, parabolic inlet + 2 % noise, smooth start
+    over 8000 steps), 40 000 steps averaged over steps 15 001-40 000: FP32 and
+    FP16-shifted <u_z> against the FP64 GPU run, region by region
+    (check_statistics); FP64 statistics accumulators throughout."""
     name = "nozzle_re6500_144x144x1200"
-    ref = nozzle_profile_run(lbm, name, "fp32", 50000, 25000)
-    assert ref[3] == 25000
-    check_statistics(name, ref, nozzle_profile_run(lbm, name, "fp16s", 50000, 25000))
+    ref, n = nozzle_stats_run(lbm, name, "fp64", 40000, 15000)
+    assert n == 25000
+    floor = nozzle_stats_run(lbm, name, "fp32", 40000, 15000, seed=3)[0]
+    runs = {p: nozzle_stats_run(lbm, name, p, 40000, 15000)[0] for p in ("fp32", "fp16s")}
+    check_statistics(name, ref, runs, floor)

@@ -1,9 +1,10 @@
 """The two FP32 / FP16S fluid kernels against the FP64 oracle (GPU required).
 
 With the default ghost rates and 32-bit offsets, FP32 and FP16S lattices run
-the staged fluid kernel (tiles of up to 32 consecutive cells of a row, inputs
-copied to shared memory ahead of use); LBM_FLUID_KERNEL=chunk, read when a
-context is created, runs the chunk kernel instead.  Both must meet the
+the tile fluid kernel (one warp per tile of up to 32 consecutive cells of a
+row; tiles of 32 fluid cells without wall links store through shared
+memory); LBM_FLUID_KERNEL=chunk, read when a context is created, runs the
+chunk kernel instead.  Both must meet the
 method's tolerances on geometries that exercise every path: walls in every
 direction and ragged rows (general tiles), long wall-free rows (fast tiles),
 inlet/outlet nodes with noise, periodic rows, both row axes, and the fused
@@ -34,7 +35,7 @@ def lbm():
     return m
 
 
-@pytest.fixture(params=["staged", "chunk"])
+@pytest.fixture(params=["tile", "chunk"])
 def kernel(request, monkeypatch):
     if request.param == "chunk":
         monkeypatch.setenv("LBM_FLUID_KERNEL", "chunk")
@@ -89,7 +90,7 @@ def test_periodic_box_rows_wrap(orc, lbm, kernel, precision):
 
 
 def test_statistics_and_health_check(orc, lbm, kernel):
-    """Fused statistics sampling and the health reduction on the staged and
+    """Fused statistics sampling and the health reduction on the tile and
     chunk kernels: FP32 sums of u_z against the oracle's per-step moments, the
     health record against lbm_get_totals."""
     flags = long_channel()
