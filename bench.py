@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--row-axis", choices=["auto", "x", "z"], default="auto",
                     help="axis of the storage rows (auto: z for the nozzles, the flow axis)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-walls", action="store_true",
+                    help="skip the smooth-surface wall (interpolated bounce-back) timing")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-stream", choices=["scaled", "full"], default="scaled",
                     help="full: the request mix at its full sizes (d 8-48, 2000-20000 steps; minutes)")
@@ -242,13 +244,15 @@ def timed_regions(torch, stream, run_region, steps, min_seconds, dist=None, devi
 
 
 def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup, min_seconds, dist=None,
-                   sampler=None, device="cpu", row_axis="auto"):
+                   sampler=None, device="cpu", row_axis="auto", wall_q=None):
     """Median milliseconds of a K-step region of one precision (max over
-    ranks is taken by the caller)."""
+    ranks is taken by the caller).  wall_q: (cells, q) of lbm_set_wall_q."""
     from paper_2204_10566_gb300 import inputs as I
 
     G = lbm.Lattice(flags, precision, periodic=periodic, row_axis=row_axis)
     G.set_params(**params)
+    if wall_q is not None:
+        G.set_wall_q(*wall_q)
     n = G.n_active
     G.init_fields(I.random_density_field(n, 0.001, 3), I.random_velocity_field(n, 0.01, 4))
     G.step(warmup).sync()
@@ -509,6 +513,24 @@ def ours_arm(args):
         by_prec[p] = {"value": world * n_p * steps / (ms_p * 1e-3) / 1e6, "unit": UNIT, "steps": steps,
                       "ms_per_step": ms_p / steps, "roofline": roof, "timing": timing_p}
 
+    by_walls = None
+    if not args.no_walls and w["kind"] == "nozzle":
+        # the paper's wall treatment: Bouzidi interpolation on the smooth surface
+        from paper_2204_10566_gb300 import inputs as I
+
+        wq = I.nozzle_wall_q(w["D"], w["d"], w["L_total"], flags=flags)
+        by_walls = {"walls": "interpolated bounce-back on the smooth nozzle surface (lbm_set_wall_q)",
+                    "wall_cells": int(wq[0].size)}
+        for p in [q for q in precisions if q != "fp64"]:
+            n_w, ms_w, _, _, timing_w = time_precision(lbm, torch, flags, params, periodic, p, args.steps,
+                                                       args.warmup, 0.5 * args.min_seconds, dist, None,
+                                                       device="cuda", row_axis=args.row_axis, wall_q=wq)
+            ms_w = aggregate_replicas(ms_w, n_w, args.steps, dist, device="cuda")[0]
+            v_w = world * n_w * args.steps / (ms_w * 1e-3) / 1e6
+            halfway = value if p == head else by_prec[p]["value"]
+            by_walls[p] = {"value": v_w, "unit": UNIT, "ms_per_step": ms_w / args.steps,
+                           "vs_halfway_walls": v_w / halfway, "timing": timing_w}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -540,6 +562,7 @@ def ours_arm(args):
                      "kernel": "k_step<%s>" % head,
                      "bytes_per_cell": algorithmic_bytes_per_cell(head)},
         "by_precision": by_prec,
+        "by_walls": by_walls,
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step(flags, periodic, head),
         "timing": dict(timing, note="gpu_launches counts the kernels of one timed K-step region"),

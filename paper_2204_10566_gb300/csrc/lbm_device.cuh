@@ -131,11 +131,34 @@ template <int AX>
 __host__ __device__ constexpr int line_pop(int j, int k) { return AX == 0 ? 3 * j + k : j + 9 * k; }
 
 // 1-D Gauss-Hermite weights of the third-order quadrature (Appendix A).
+// Scalar type of R (F2 holds two FP32 values).
 template <class R>
-__device__ __forceinline__ R w1(int c) { return c == 0 ? R(2) / R(3) : R(1) / R(6); }
+struct ScalarOf {
+    using type = R;
+};
+template <>
+struct ScalarOf<struct F2> {
+    using type = float;
+};
 
 template <class R>
-__device__ __forceinline__ R theta0() { return R(1) / R(3); }
+__device__ __forceinline__ R w1(int c) {
+    using X = typename ScalarOf<R>::type;
+    return R(c == 0 ? X(2) / X(3) : X(1) / X(6));
+}
+
+template <class R>
+__device__ __forceinline__ R theta0() {
+    using X = typename ScalarOf<R>::type;
+    return R(X(1) / X(3));
+}
+
+// The rational constant a / b in the scalar precision of R.
+template <class R>
+__device__ __forceinline__ R cst(int a, int b) {
+    using X = typename ScalarOf<R>::type;
+    return R(X(a) / X(b));
+}
 
 // 1-D inverse-transform columns at velocity u (T_1D(u)^-1, column k = g_k):
 //   g0(c) = w(c) + d(c), d(0) = -u^2, d(+-1) = (u^2 +- u)/2
@@ -235,6 +258,22 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
+// Two cells' FP32 values on the packed pipe: every arithmetic operation of
+// the collision applies to both lanes with one instruction.
+struct F2 {
+    float2 v;
+    F2() = default;
+    __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ explicit F2(float2 w) : v(w) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, bc2(-1.0f), a.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2 &operator*=(F2 &a, F2 b) { return a = a * b; }
+__device__ __forceinline__ F2 recip(F2 x) { return F2(make_float2(__frcp_rn(x.v.x), __frcp_rn(x.v.y))); }
+
 // Shared inputs of the per-line inverse (see collide_ghost1).
 struct PairCoef {
     float Axx, Ayy, Azz, Axy, Axz, Ayz, rho_o, drho_o, ux, ux2h, uxh;
@@ -243,7 +282,7 @@ struct PairCoef {
 // One line (cy, cz) of the inverse: f*_i - w_i for cx = -1, 0, +1.
 template <class R, int J, class Out>
 __device__ __forceinline__ void inverse_line(R Axx, R Ayy, R Azz, R Axy, R Axz, R Ayz, R rho_o, R drho_o, R ux, R ux2h,
-                                             R uxh, const Axis<R> &Y, const Axis<R> &Z, R (&d)[27], const Out *sink) {
+                                             R uxh, const Axis<R> &Y, const Axis<R> &Z, const Out &sink) {
     constexpr int cy = J % 3 - 1, cz = J / 3 - 1;
     const R h = R(0.5);
     const R wy = w1<R>(cy);
@@ -255,16 +294,10 @@ __device__ __forceinline__ void inverse_line(R Axx, R Ayy, R Azz, R Axy, R Axz, 
     const R B2 = Axx * E;
     const R Bw = drho_o * (wy * w1<R>(cz)) + rho_o * D + C0;
     const R Bd = rho_o * E + C0;
-    const R v0 = R(2) / R(3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
-    const R S = R(1) / R(6) * Bw + ux2h * Bd + ux * B1 + h * B2;
+    const R v0 = cst<R>(2, 3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
+    const R S = cst<R>(1, 6) * Bw + ux2h * Bd + ux * B1 + h * B2;
     const R A = uxh * Bd + h * B1;
-    if (sink)
-        (*sink)(J, S - A, v0, S + A);
-    else {
-        d[3 * J] = S - A;
-        d[3 * J + 1] = v0;
-        d[3 * J + 2] = S + A;
-    }
+    sink(J, S - A, v0, S + A);
 }
 
 // Two lines of the inverse at once.  The pair differs along one axis ("v",
@@ -277,7 +310,7 @@ __device__ __forceinline__ void inverse_line(R Axx, R Ayy, R Azz, R Axy, R Axz, 
 // with the same Bw, Bd, v0, S, A as the scalar line.
 template <int JA, int JB, class Out>
 __device__ __forceinline__ void inverse_pair(const PairCoef &c, const Axis<float> &Y, const Axis<float> &Z,
-                                             float (&d)[27], const Out *sink) {
+                                             const Out &sink) {
     constexpr bool YV = (JA / 3) == (JB / 3);  // same cz: y varies
     constexpr int cf = YV ? JA / 3 - 1 : JA % 3 - 1;  // fixed axis velocity
     const Axis<float> &V = YV ? Y : Z;
@@ -300,24 +333,10 @@ __device__ __forceinline__ void inverse_pair(const PairCoef &c, const Axis<float
     const float2 S = __ffma2_rn(bc2(1.0f / 6.0f), Bw, __fadd2_rn(t, hB2));
     const float2 A = __ffma2_rn(bc2(c.uxh), Bd, hB1);
     const float2 om = __ffma2_rn(bc2(-1.0f), A, S), op = __fadd2_rn(S, A);
-    if (sink) {
-        (*sink)(JA, om.x, o0.x, op.x);
-        (*sink)(JB, om.y, o0.y, op.y);
-    } else {
-        d[3 * JA] = om.x;
-        d[3 * JA + 1] = o0.x;
-        d[3 * JA + 2] = op.x;
-        d[3 * JB] = om.y;
-        d[3 * JB + 1] = o0.y;
-        d[3 * JB + 2] = op.y;
-    }
+    sink(JA, om.x, o0.x, op.x);
+    sink(JB, om.y, o0.y, op.y);
 }
 
-// Collision with the default ghost rates (all 1).  d holds f_i - w_i on entry
-// and f*_i - w_i on exit; rho, u receive the (conserved) moments.  With
-// SCALED, d holds (f_i - w_i) / in_scale on entry and (f*_i - w_i) * out_scale
-// on exit: the scale is applied to the ten moments and to the eight output
-// coefficients instead of to the 54 populations.
 // Writes a line of three outputs (cx = -1, 0, +1 of line j) back into d.
 template <class R>
 struct ToArray {
@@ -340,14 +359,22 @@ struct ToArrayStress {
     __device__ __forceinline__ void operator()(int j, R vm, R v0, R vp) const { ToArray<R>{d}(j, vm, v0, vp); }
 };
 
-template <class R, bool SCALED = false, class Out = ToArray<R>>
-__device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &ux, R &uy, R &uz,
-                                               R in_scale = R(1), R out_scale = R(1), const Out *sink = nullptr) {
-    // x-pass of the moment cascade: per (cy, cz) line, sums weighted by 1, cx, cx^2.
+// Identity conversion of a collision input.
+struct SameInput {
+    template <class R>
+    __device__ __forceinline__ R operator()(R v) const { return v; }
+};
+
+// Moment sums of the default-rate collision from its 27 inputs (cvt turns an
+// input into R): m = drho, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz, the
+// sums of (f - w) weighted by 1, c, and c_a c_b.  The x-pass sums each
+// (cy, cz) line with weights 1, cx, cx^2; the other axes follow.
+template <class R, class In, class Cvt>
+__device__ __forceinline__ void ghost1_sums(const In (&d)[27], const Cvt &cvt, R (&m)[10]) {
     R s0[9], s1[9], s2[9];
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        const R a = d[3 * j], b = d[3 * j + 1], c = d[3 * j + 2];
+        const R a = cvt(d[3 * j]), b = cvt(d[3 * j + 1]), c = cvt(d[3 * j + 2]);
         s0[j] = (a + b) + c;
         s1[j] = c - a;
         s2[j] = c + a;
@@ -371,6 +398,21 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
         }
         if (cy != 0 && cz != 0) pyz += (cy * cz) > 0 ? s0[j] : -s0[j];
     }
+    m[0] = drho, m[1] = jx, m[2] = jy, m[3] = jz, m[4] = pxx;
+    m[5] = pyy, m[6] = pzz, m[7] = pxy, m[8] = pxz, m[9] = pyz;
+}
+
+// The rest of the default-rate collision from the moment sums: rho, u, the
+// six second-order central Hermite moments, their relaxation, and the
+// inverse transform, line by line into sink(j, f*_{3j} - w, f*_{3j+1} - w,
+// f*_{3j+2} - w).  With SCALED the sums are of (f - w) / in_scale and the
+// outputs are (f* - w) * out_scale: the scales act on the ten moments and
+// the eight output coefficients instead of on the 54 populations.
+template <class R, bool SCALED, class Out>
+__device__ __forceinline__ void ghost1_finish(const R (&m)[10], R omega, R &rho, R &ux, R &uy, R &uz, R in_scale,
+                                              R out_scale, const Out &sink) {
+    R drho = m[0], jx = m[1], jy = m[2], jz = m[3], pxx = m[4], pyy = m[5], pzz = m[6], pxy = m[7], pxz = m[8],
+      pyz = m[9];
     if constexpr (SCALED) {
         drho *= in_scale;
         jx *= in_scale;
@@ -395,7 +437,7 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
     const R rho_o = SCALED ? rho * out_scale : rho, drho_o = SCALED ? drho * out_scale : drho;
     const R a2[6] = {pxx - rho * ux * ux - th * drho, pyy - rho * uy * uy - th * drho, pzz - rho * uz * uz - th * drho,
                      pxy - rho * ux * uy,            pxz - rho * ux * uz,            pyz - rho * uy * uz};
-    if (sink) sink->moments(omega, a2);
+    sink.moments(omega, a2);
     const R Axx = k * a2[0];
     const R Ayy = k * a2[1];
     const R Azz = k * a2[2];
@@ -415,11 +457,11 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
         // Lines in pairs on the packed FP32 pipe (two lanes per instruction):
         // (cy = -1, +1) at each cz, then (cz = -1, +1) at cy = 0; line 4 alone.
         const PairCoef c{Axx, Ayy, Azz, Axy, Axz, Ayz, rho_o, drho_o, ux, ux2h, uxh};
-        inverse_pair<0, 2>(c, Y, Z, d, sink);
-        inverse_pair<3, 5>(c, Y, Z, d, sink);
-        inverse_pair<6, 8>(c, Y, Z, d, sink);
-        inverse_pair<1, 7>(c, Y, Z, d, sink);
-        inverse_line<R, 4>(Axx, Ayy, Azz, Axy, Axz, Ayz, rho_o, drho_o, ux, ux2h, uxh, Y, Z, d, sink);
+        inverse_pair<0, 2>(c, Y, Z, sink);
+        inverse_pair<3, 5>(c, Y, Z, sink);
+        inverse_pair<6, 8>(c, Y, Z, sink);
+        inverse_pair<1, 7>(c, Y, Z, sink);
+        inverse_line<R, 4>(Axx, Ayy, Azz, Axy, Axz, Ayz, rho_o, drho_o, ux, ux2h, uxh, Y, Z, sink);
         return;
     }
 #endif
@@ -436,15 +478,27 @@ __device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &u
         const R Bw = drho_o * (wy * w1<R>(cz)) + rho_o * D + C0;
         const R Bd = rho_o * E + C0;
         // cx = 0: w = 2/3, d = -ux^2, g1 = -2 ux, g2 = -1
-        const R v0 = R(2) / R(3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
+        const R v0 = cst<R>(2, 3) * Bw - R(2) * (ux2h * Bd + ux * B1) - B2;
         // cx = +-1: w = 1/6, d = (ux^2 +- ux)/2, g1 = ux +- 1/2, g2 = 1/2
-        const R S = R(1) / R(6) * Bw + ux2h * Bd + ux * B1 + h * B2;
+        const R S = cst<R>(1, 6) * Bw + ux2h * Bd + ux * B1 + h * B2;
         const R A = uxh * Bd + h * B1;
-        if (sink)
-            (*sink)(j, S - A, v0, S + A);  // the line's outputs leave registers at once
-        else
-            ToArray<R>{d}(j, S - A, v0, S + A);
+        sink(j, S - A, v0, S + A);  // the line's outputs leave registers at once
     }
+}
+
+// Collision with the default ghost rates (all 1).  d holds f_i - w_i on entry;
+// the post-collision f*_i - w_i go to the sink line by line, or back into d
+// without one.  rho, u receive the (conserved) moments.  With SCALED, d holds
+// (f_i - w_i) / in_scale and the outputs are (f*_i - w_i) * out_scale.
+template <class R, bool SCALED = false, class Out = ToArray<R>>
+__device__ __forceinline__ void collide_ghost1(R (&d)[27], R omega, R &rho, R &ux, R &uy, R &uz,
+                                               R in_scale = R(1), R out_scale = R(1), const Out *sink = nullptr) {
+    R m[10];
+    ghost1_sums(d, SameInput{}, m);
+    if (sink)
+        ghost1_finish<R, SCALED>(m, omega, rho, ux, uy, uz, in_scale, out_scale, *sink);
+    else
+        ghost1_finish<R, SCALED>(m, omega, rho, ux, uy, uz, in_scale, out_scale, ToArray<R>{d});
 }
 
 // 1-D forward central Hermite factor h_k(c - u): 1, c - u, (c - u)^2 - theta0.
@@ -1264,6 +1318,91 @@ __global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step_tile
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
 
+// ------------------------------------------------ pair fluid kernel (FP16S)
+//
+// Fast tiles of an FP16S lattice (32 fluid cells of a row without wall links
+// or wrap-around copies) with two adjacent cells per thread: 16 threads per
+// tile, thread k updates cells x = p0 + 2k and x + 1.  The collision runs on
+// the packed FP32 pipe across the pair (one instruction for both cells); its
+// 27 inputs stay FP16 pairs until the moment pass converts them; the pull of
+// each line along the row (c = 0 along the row axis) is one aligned 32-bit
+// load of both cells' values, the other two pulls two 16-bit loads; and each
+// output leaves as one 32-bit store of both cells' own slots.  Every thread
+// holds two cells' work, so the kernel runs at half the occupancy of the
+// one-cell kernels with the same bytes in flight per SM.
+#ifndef LBM_PAIR_MIN_BLOCKS
+#define LBM_PAIR_MIN_BLOCKS 4
+#endif
+
+struct Half2ToF2 {
+    __device__ __forceinline__ F2 operator()(__half2 h) const { return F2(__half22float2(h)); }
+};
+
+// Pull gather of the pair (x, x + 1), x even: d[i] = FP16 pulls of both cells.
+template <int AX>
+__device__ __forceinline__ void gather_pair(const StepArgs &a, const int (&nb)[9], int x, __half2 (&d)[27]) {
+    const __half *fin = static_cast<const __half *>(a.fin);
+    const uint32_t st = (uint32_t)a.stride;
+    constexpr int dk = line_pop<AX>(0, 1) - line_pop<AX>(0, 0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const __half *pj = fin + ((uint32_t)line_pop<AX>(j, 0) * st + (uint32_t)(nb[j] + x));
+        // c_row = -1: pulls from x + 1, x + 2
+        d[line_pop<AX>(j, 0)] = __halves2half2(__ldg(pj + 1), __ldg(pj + 2));
+        // c_row = 0: pulls from x, x + 1, one aligned 32-bit load
+        d[line_pop<AX>(j, 1)] = __ldg(reinterpret_cast<const __half2 *>(pj + dk * st));
+        // c_row = +1: pulls from x - 1, x
+        d[line_pop<AX>(j, 2)] = __halves2half2(__ldg(pj + 2 * dk * st - 1), __ldg(pj + 2 * dk * st));
+    }
+}
+
+// Output sink of the pair kernel: both cells' values of population i as one
+// FP16 pair at their own slots (slot even), already scaled by the collision.
+struct PairStore {
+    const StepArgs &a;
+    int slot;
+    __device__ __forceinline__ void moments(F2 omega, const F2 (&a2)[6]) const {
+        if ((a.flags & (STEP_STATS | STEP_STATS_FULL)) != (STEP_STATS | STEP_STATS_FULL)) return;
+        float ax[6], ay[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ax[q] = a2[q].v.x, ay[q] = a2[q].v.y;
+        record_stress(a, slot, omega.v.x, ax);
+        record_stress(a, slot + 1, omega.v.y, ay);
+    }
+    __device__ __forceinline__ void operator()(int j, F2 vm, F2 v0, F2 vp) const {
+        const uint32_t st = (uint32_t)a.stride;
+        __half *pj = static_cast<__half *>(a.fout) + ((uint32_t)(3 * j) * st + (uint32_t)slot);
+        *reinterpret_cast<__half2 *>(pj) = __float22half2_rn(vm.v);
+        *reinterpret_cast<__half2 *>(pj + st) = __float22half2_rn(v0.v);
+        *reinterpret_cast<__half2 *>(pj + 2 * st) = __float22half2_rn(vp.v);
+    }
+};
+
+template <int AX>
+__global__ void __launch_bounds__(STEP_THREADS, LBM_PAIR_MIN_BLOCKS) k_step_pairs(const StepArgs a) {
+    const int g = (int)(blockIdx.x * STEP_THREADS + threadIdx.x);
+    const int t = g >> 4, k = g & 15;  // fast tile, pair within it
+    double hv[6] = {0, 0, 0, 0, 0, 0};
+    if (t < a.nfast) {
+        const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * ((size_t)a.ntiles + t);
+        const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+        const int nb[9] = {r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+        const int x = (int)((uint32_t)r0.x & CHUNK_X0_MASK) + 2 * k, slot = nb[4] + x;
+        __half2 d[27];
+        gather_pair<AX>(a, nb, x, d);
+        F2 m[10], rho, ux, uy, uz;
+        ghost1_sums(d, Half2ToF2{}, m);
+        const PairStore sink{a, slot};
+        ghost1_finish<F2, true>(m, F2(a.pf.omega), rho, ux, uy, uz, F2(a.inv_scale), F2(a.scale), sink);
+        double h0[6] = {0, 0, 0, 0, 0, 0}, h1[6] = {0, 0, 0, 0, 0, 0};
+        record_cell(a, slot, rho.v.x, ux.v.x, uy.v.x, uz.v.x, h0);
+        record_cell(a, slot + 1, rho.v.y, ux.v.y, uy.v.y, uz.v.y, h1);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) hv[q] = q == 4 ? fmax(h0[q], h1[q]) : h0[q] + h1[q];
+    }
+    if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials + (size_t)tile_blocks(a.ntiles) * REDUCE_SLOTS);
+}
+
 // ---------------------------------------------------------- utility kernels
 
 template <int P>
@@ -1472,6 +1611,8 @@ void launch_step_ax(const StepArgs &a, cudaStream_t s) {
     if constexpr (G && !WD && P != 0) {
         if (a.tiles) {  // the tile fluid kernel; inlet/outlet nodes and wall cells in launches of their own
             if (a.ntiles > 0) k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
+            if constexpr (P == 2)  // FP16S fast tiles, two cells per thread
+                if (a.nfast > 0) k_step_pairs<AX><<<pair_blocks(a.nfast), STEP_THREADS, 0, s>>>(a);
             if (a.nwnodes > 0)
                 k_wall<P, G, WD, AX><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
             if (bb > 0) k_boundary<P, G, WD, AX><<<bb, STEP_THREADS, 0, s>>>(a);

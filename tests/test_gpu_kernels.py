@@ -3,8 +3,10 @@
 With the default ghost rates and 32-bit offsets, FP32 and FP16S lattices run
 the tile fluid kernel (one warp per tile of up to 32 consecutive cells of a
 row; tiles of 32 fluid cells without wall links store through shared
-memory); LBM_FLUID_KERNEL=chunk, read when a context is created, runs the
-chunk kernel instead.  Both must meet the
+memory), and FP16S runs those fast tiles on the pair kernel (two adjacent
+cells per thread on the packed FP32 pipe).  LBM_FLUID_KERNEL, read when a
+context is created, selects "tile" (no pair kernel) or "chunk" (the chunk
+kernel) instead.  Both must meet the
 method's tolerances on geometries that exercise every path: walls in every
 direction and ragged rows (general tiles), long wall-free rows (fast tiles),
 inlet/outlet nodes with noise, periodic rows, both row axes, and the fused
@@ -35,12 +37,12 @@ def lbm():
     return m
 
 
-@pytest.fixture(params=["tile", "chunk"])
+@pytest.fixture(params=["default", "tile", "chunk"])
 def kernel(request, monkeypatch):
-    if request.param == "chunk":
-        monkeypatch.setenv("LBM_FLUID_KERNEL", "chunk")
-    else:
+    if request.param == "default":  # FP16S fast tiles on the pair kernel
         monkeypatch.delenv("LBM_FLUID_KERNEL", raising=False)
+    else:
+        monkeypatch.setenv("LBM_FLUID_KERNEL", request.param)
     return request.param
 
 
