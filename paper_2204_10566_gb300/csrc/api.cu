@@ -38,10 +38,10 @@ struct lbm_ctx {
     int64_t n_wnodes = 0;
     int2 *d_chunks_wall = nullptr;   // chunk records without those cells (the fluid kernel's list)
     int32_t *d_tiles_wall = nullptr; // tile records without those cells
-    int64_t n_tiles_wall = 0, n_tiles_wall_general = 0;
+    int64_t n_tiles_wall = 0;
     bool wide_offsets = false;       // LBM_WIDE_OFFSETS=1 at creation: the 64-bit offset kernels always
     bool chunk_kernel = false;       // LBM_FLUID_KERNEL=chunk at creation: no tile fluid kernel
-    bool pair_kernel = true;         // FP16S fast tiles two cells per thread (LBM_FLUID_KERNEL=tile: off)
+    bool pair_kernel = true;         // FP16S tiles two cells per thread (LBM_FLUID_KERNEL=tile: off)
     int32_t *d_tiles = nullptr;      // tile records of the tile fluid kernel
     double *d_partials = nullptr;
     double *d_health = nullptr;
@@ -131,7 +131,7 @@ void release_wall_q(lbm_ctx *c) {
     if (c->d_tiles_wall) dev_free(c, c->d_tiles_wall, (size_t)c->n_tiles_wall * TILE_INTS * 4);
     c->d_chunks_wall = nullptr;
     c->d_tiles_wall = nullptr;
-    c->n_tiles_wall = c->n_tiles_wall_general = 0;
+    c->n_tiles_wall = 0;
     c->d_wall_qidx = nullptr;
     c->d_wall_q = nullptr;
     c->d_wnodes = nullptr;
@@ -214,14 +214,11 @@ int64_t tile_count(const lbm_ctx *c) {
 bool tiled(const lbm_ctx *c) {
     return c->desc.precision != LBM_FP64 && c->ghost1 && !wide_offsets(c) && !c->chunk_kernel && tile_count(c) > 0;
 }
-int64_t general_tile_count(const lbm_ctx *c) { return c->d_tiles_wall ? c->n_tiles_wall_general : c->idx.tiles_general; }
-// Tiles of the tile kernel, and FP16S fast tiles of the pair kernel.
-int64_t tile_kernel_tiles(const lbm_ctx *c) {
-    return c->desc.precision == LBM_FP16S && c->pair_kernel ? general_tile_count(c) : tile_count(c);
-}
-int64_t pair_kernel_tiles(const lbm_ctx *c) { return tile_count(c) - tile_kernel_tiles(c); }
+// FP16S tiles run on the pair kernel, FP32 tiles on the tile kernel.
+bool pairs(const lbm_ctx *c) { return c->desc.precision == LBM_FP16S && c->pair_kernel; }
 int fluid_partials(const lbm_ctx *c) {
-    return tiled(c) ? tile_blocks(tile_kernel_tiles(c)) + pair_blocks(pair_kernel_tiles(c)) : c->fluid_blocks;
+    if (!tiled(c)) return c->fluid_blocks;
+    return pairs(c) ? pair_blocks(tile_count(c)) : tile_blocks(tile_count(c));
 }
 int step_partials(const lbm_ctx *c) {
     return fluid_partials(c) + node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(c->n_wnodes);
@@ -229,8 +226,7 @@ int step_partials(const lbm_ctx *c) {
 // Partial-sum capacity for either fluid kernel, the wall cells and lbm_get_totals.
 int partial_capacity(const lbm_ctx *c, int64_t n_wnodes) {
     const int nodes = node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(n_wnodes);
-    // the tile kernel and the pair kernel together need at most a block per tile
-    const int tiles = (int)std::max<int64_t>((int64_t)c->idx.tiles.size() / TILE_INTS, c->n_tiles_wall);
+    const int tiles = tile_blocks(std::max<int64_t>((int64_t)c->idx.tiles.size() / TILE_INTS, c->n_tiles_wall));
     return std::max({c->fluid_blocks + nodes, tiles + nodes, node_blocks(c->idx.n_active)});
 }
 
@@ -304,8 +300,8 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     const bool wide = wide_offsets(c);
     if (tiled(c)) {
         a.tiles = c->d_tiles_wall ? c->d_tiles_wall : c->d_tiles;
-        a.ntiles = (int32_t)tile_kernel_tiles(c);
-        a.nfast = (int32_t)pair_kernel_tiles(c);
+        a.ntiles = (int32_t)tile_count(c);
+        a.pairs = pairs(c) ? 1 : 0;
     }
     const int key = (c->ghost1 ? 2 : 0) + (wide ? 1 : 0);
     if (c->prefetch_key != key) {
@@ -478,10 +474,9 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
             if (((lanes >> l) & 1u) && is_wall[(size_t)(base + x0 + l)]) lanes &= ~(1u << l);
         ch.y = (int)((uint32_t)x0 | (lanes << CHUNK_LANES_SHIFT));
     }
-    int64_t general = 0;
     const std::vector<int32_t> tiles =
         wn.empty() ? std::vector<int32_t>()
-                   : build_tiles(chunks, c->idx.row_nb, c->idx.mask, c->idx.n_row, periodic_rows(c) != 0, &general);
+                   : build_tiles(chunks, c->idx.row_nb, c->idx.mask, c->idx.n_row, periodic_rows(c) != 0);
     c->d_wall_qidx = (int32_t *)dev_alloc(c, qidx.size() * 4);
     c->d_wall_q = (uint8_t *)dev_alloc(c, rec.size());
     c->n_wall_q = n;
@@ -490,7 +485,6 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     if (!wn.empty()) c->d_chunks_wall = (int2 *)dev_alloc(c, chunks.size() * 8);
     if (!wn.empty()) {
         c->n_tiles_wall = (int64_t)tiles.size() / TILE_INTS;
-        c->n_tiles_wall_general = general;
         c->d_tiles_wall = (int32_t *)dev_alloc(c, tiles.size() * 4);
     }
     const int capacity = partial_capacity(c, c->n_wnodes);

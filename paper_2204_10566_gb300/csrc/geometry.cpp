@@ -268,14 +268,13 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
             }
         }
     if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
-    out.tiles = build_tiles(out.chunks, out.row_nb, out.mask, F.np, F.pp, &out.tiles_general);
+    out.tiles = build_tiles(out.chunks, out.row_nb, out.mask, F.np, F.pp);
     return "";
 }
 
 std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
-                                 const std::vector<uint32_t> &mask, int n_row, bool periodic_row,
-                                 int64_t *n_general) {
-    std::vector<int32_t> tiles, fast_tiles;
+                                 const std::vector<uint32_t> &mask, int n_row, bool periodic_row) {
+    std::vector<int32_t> tiles;
     int row = -1, p0 = 0, n = 0;  // the open tile
     uint32_t fluid = 0, present = 0;
     auto flush = [&]() {
@@ -284,11 +283,10 @@ std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vec
         bool fast = fluid == 0xFFFFFFFFu && !(periodic_row && (p0 == 0 || p0 + 31 >= n_row - 1));
         const int32_t base = row_nb[(size_t)row * ROW_RECORD_INTS + 4];
         for (int l = 0; fast && l < 32; ++l) fast = (mask[(size_t)(base + p0 + l)] & LINK_MASK) == 0u;
-        std::vector<int32_t> &dst = fast ? fast_tiles : tiles;
-        dst.push_back((int32_t)((uint32_t)p0 | (fast ? TILE_FAST : 0u)));
-        dst.push_back((int32_t)fluid);
-        dst.push_back((int32_t)present);
-        for (int j = 0; j < 9; ++j) dst.push_back(row_nb[(size_t)row * ROW_RECORD_INTS + j]);
+        tiles.push_back((int32_t)((uint32_t)p0 | (fast ? TILE_FAST : 0u)));
+        tiles.push_back((int32_t)fluid);
+        tiles.push_back((int32_t)present);
+        for (int j = 0; j < 9; ++j) tiles.push_back(row_nb[(size_t)row * ROW_RECORD_INTS + j]);
         n = 0;
     };
     for (const int2 &c : chunks) {
@@ -305,8 +303,6 @@ std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vec
         ++n;
     }
     flush();
-    *n_general = (int64_t)tiles.size() / TILE_INTS;
-    tiles.insert(tiles.end(), fast_tiles.begin(), fast_tiles.end());
     return tiles;
 }
 

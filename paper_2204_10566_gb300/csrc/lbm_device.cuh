@@ -1320,18 +1320,19 @@ __global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step_tile
 
 // ------------------------------------------------ pair fluid kernel (FP16S)
 //
-// Fast tiles of an FP16S lattice (32 fluid cells of a row without wall links
-// or wrap-around copies) with two adjacent cells per thread: 16 threads per
-// tile, thread k updates cells x = p0 + 2k and x + 1.  The collision runs on
-// the packed FP32 pipe across the pair (one instruction for both cells); its
-// 27 inputs stay FP16 pairs until the moment pass converts them; the pull of
-// each line along the row (c = 0 along the row axis) is one aligned 32-bit
-// load of both cells' values, the other two pulls two 16-bit loads; and each
-// output leaves as one 32-bit store of both cells' own slots.  Every thread
-// holds two cells' work, so the kernel runs at half the occupancy of the
-// one-cell kernels with the same bytes in flight per SM.
+// The tiles of an FP16S lattice with two adjacent cells per thread: 16
+// threads per tile, thread k updates cells x = p0 + 2k and x + 1.  The
+// collision runs on the packed FP32 pipe across the pair (one instruction
+// for both cells); its 27 inputs stay FP16 pairs until the moment pass
+// converts them; the pull of each line along the row (c = 0 along the row
+// axis) is one aligned 32-bit load of both cells' values, the other two are
+// two 16-bit loads.  A fast tile (32 fluid cells, no wall link, no
+// wrap-around copy) writes each output as one 32-bit store of both cells'
+// own slots; other tiles go through a per-cell line sink (PairLineStore).
+// Every thread holds two cells, so the kernel runs at fewer resident warps
+// than the one-cell kernels with the same bytes in flight per SM.
 #ifndef LBM_PAIR_MIN_BLOCKS
-#define LBM_PAIR_MIN_BLOCKS 4
+#define LBM_PAIR_MIN_BLOCKS 5
 #endif
 
 struct Half2ToF2 {
@@ -1356,18 +1357,24 @@ __device__ __forceinline__ void gather_pair(const StepArgs &a, const int (&nb)[9
     }
 }
 
-// Output sink of the pair kernel: both cells' values of population i as one
-// FP16 pair at their own slots (slot even), already scaled by the collision.
+// Viscous stress of the pair's fluid cells (statistics sample steps).
+__device__ __forceinline__ void record_stress_pair(const StepArgs &a, int slot, F2 omega, const F2 (&a2)[6],
+                                                   bool fluid0, bool fluid1) {
+    if ((a.flags & (STEP_STATS | STEP_STATS_FULL)) != (STEP_STATS | STEP_STATS_FULL)) return;
+    float ax[6], ay[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) ax[q] = a2[q].v.x, ay[q] = a2[q].v.y;
+    if (fluid0) record_stress(a, slot, omega.v.x, ax);
+    if (fluid1) record_stress(a, slot + 1, omega.v.y, ay);
+}
+
+// Output sink of a fast tile: both cells' values of population i as one FP16
+// pair at their own slots (slot even), already scaled by the collision.
 struct PairStore {
     const StepArgs &a;
     int slot;
     __device__ __forceinline__ void moments(F2 omega, const F2 (&a2)[6]) const {
-        if ((a.flags & (STEP_STATS | STEP_STATS_FULL)) != (STEP_STATS | STEP_STATS_FULL)) return;
-        float ax[6], ay[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) ax[q] = a2[q].v.x, ay[q] = a2[q].v.y;
-        record_stress(a, slot, omega.v.x, ax);
-        record_stress(a, slot + 1, omega.v.y, ay);
+        record_stress_pair(a, slot, omega, a2, true, true);
     }
     __device__ __forceinline__ void operator()(int j, F2 vm, F2 v0, F2 vp) const {
         const uint32_t st = (uint32_t)a.stride;
@@ -1378,29 +1385,105 @@ struct PairStore {
     }
 };
 
+// Output sink of the other tiles: LineStore's stores for each cell of the
+// pair (own slots by the own masks, one 32-bit store when both cells take
+// population i; ghost slots of each cell's wall links; wrap-around copies).
+template <int AX>
+struct PairLineStore {
+    const StepArgs &a;
+    const int (&nb)[9];
+    int x, slot;
+    uint32_t links0, links1, own0, own1;
+    __device__ __forceinline__ void put(int i, int s, float v) const {
+        static_cast<__half *>(a.fout)[elem<false>(i, a.stride, s)] = __float2half_rn(v);
+    }
+    __device__ __forceinline__ void moments(F2 omega, const F2 (&a2)[6]) const {
+        record_stress_pair(a, slot, omega, a2, (own0 & OWN_FLUID) != 0u, (own1 & OWN_FLUID) != 0u);
+    }
+    __device__ __forceinline__ void operator()(int j, F2 vm, F2 v0, F2 vp) const {
+        const F2 v[3] = {vm, v0, vp};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int i = 3 * j + c;
+            const bool b0 = (own0 >> i) & 1u, b1 = (own1 >> i) & 1u;
+            if (b0 && b1) {
+                *reinterpret_cast<__half2 *>(static_cast<__half *>(a.fout) + elem<false>(i, a.stride, slot)) =
+                    __float22half2_rn(v[c].v);
+            } else {
+                if (b0) put(i, slot, v[c].v.x);
+                if (b1) put(i, slot + 1, v[c].v.y);
+            }
+        }
+        const int jl = 8 - j;  // links 26 - i of this line's values sit in line 8 - j
+        if ((links0 | links1) & (7u << (3 * jl))) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k = 26 - (3 * j + c);  // wall link k takes value 3j + c
+                const int s = nb[row_line<AX>(k)] + x - c_row<AX>(k);
+                if (links0 & (1u << k)) put(k, s, v[c].v.x);
+                if (links1 & (1u << k)) put(k, s + 1, v[c].v.y);
+            }
+        }
+        if (a.periodic_row) {  // wrap-around copies across the periodic row faces
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int i = 3 * j + c;
+                if (c_row<AX>(i) == 1) {
+                    if ((own0 & OWN_FLUID) && x == a.n_row - 1) put(i, nb[4] - 1, v[c].v.x);
+                    if ((own1 & OWN_FLUID) && x + 1 == a.n_row - 1) put(i, nb[4] - 1, v[c].v.y);
+                }
+                if (c_row<AX>(i) == -1) {
+                    if ((own0 & OWN_FLUID) && x == 0) put(i, nb[4] + a.n_row, v[c].v.x);
+                }
+            }
+        }
+    }
+};
+
+// Own-slot mask of a cell for LineStore-style sinks: every population for a
+// fluid cell; for a padding or ghost slot of the tile, the populations that
+// nobody reads there (filler that completes the row-end sectors); nothing
+// for inlet/outlet slots and lanes outside the tile's chunks.
+__device__ __forceinline__ uint32_t own_mask(bool fluid, bool present, uint32_t m) {
+    return fluid ? (LINK_MASK | OWN_FLUID) : (present && ((m >> TYPE_SHIFT) & 3u) == TYPE_PAD ? (~m & LINK_MASK) : 0u);
+}
+
 template <int AX>
 __global__ void __launch_bounds__(STEP_THREADS, LBM_PAIR_MIN_BLOCKS) k_step_pairs(const StepArgs a) {
     const int g = (int)(blockIdx.x * STEP_THREADS + threadIdx.x);
-    const int t = g >> 4, k = g & 15;  // fast tile, pair within it
+    const int t = g >> 4, k = g & 15;  // tile, pair within it
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (t < a.nfast) {
-        const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * ((size_t)a.ntiles + t);
+    if (t < a.ntiles) {  // uniform over the 16 threads of the tile
+        const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * (size_t)t;
         const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
         const int nb[9] = {r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+        const bool fast = ((uint32_t)r0.x & TILE_FAST) != 0u;
         const int x = (int)((uint32_t)r0.x & CHUNK_X0_MASK) + 2 * k, slot = nb[4] + x;
+        const bool fluid0 = ((uint32_t)r0.y >> (2 * k)) & 1u, fluid1 = ((uint32_t)r0.y >> (2 * k + 1)) & 1u;
         __half2 d[27];
-        gather_pair<AX>(a, nb, x, d);
+        gather_pair<AX>(a, nb, x, d);  // every lane's pulls lie inside the buffer margins
         F2 m[10], rho, ux, uy, uz;
         ghost1_sums(d, Half2ToF2{}, m);
-        const PairStore sink{a, slot};
-        ghost1_finish<F2, true>(m, F2(a.pf.omega), rho, ux, uy, uz, F2(a.inv_scale), F2(a.scale), sink);
+        const F2 omega(a.pf.omega), in_s(a.inv_scale), out_s(a.scale);
+        if (fast) {
+            ghost1_finish<F2, true>(m, omega, rho, ux, uy, uz, in_s, out_s, PairStore{a, slot});
+        } else {
+            const bool present0 = ((uint32_t)r0.z >> (2 * k)) & 1u, present1 = ((uint32_t)r0.z >> (2 * k + 1)) & 1u;
+            const uint2 mm = present0 || present1 ? __ldg(reinterpret_cast<const uint2 *>(a.mask + slot))
+                                                  : make_uint2(0u, 0u);
+            const uint32_t m0 = present0 ? mm.x : 0u, m1 = present1 ? mm.y : 0u;
+            const PairLineStore<AX> sink{a, nb, x, slot, fluid0 ? (m0 & LINK_MASK) : 0u,
+                                         fluid1 ? (m1 & LINK_MASK) : 0u, own_mask(fluid0, present0, m0),
+                                         own_mask(fluid1, present1, m1)};
+            ghost1_finish<F2, true>(m, omega, rho, ux, uy, uz, in_s, out_s, sink);
+        }
         double h0[6] = {0, 0, 0, 0, 0, 0}, h1[6] = {0, 0, 0, 0, 0, 0};
-        record_cell(a, slot, rho.v.x, ux.v.x, uy.v.x, uz.v.x, h0);
-        record_cell(a, slot + 1, rho.v.y, ux.v.y, uy.v.y, uz.v.y, h1);
+        if (fluid0) record_cell(a, slot, rho.v.x, ux.v.x, uy.v.x, uz.v.x, h0);
+        if (fluid1) record_cell(a, slot + 1, rho.v.y, ux.v.y, uy.v.y, uz.v.y, h1);
 #pragma unroll
         for (int q = 0; q < 6; ++q) hv[q] = q == 4 ? fmax(h0[q], h1[q]) : h0[q] + h1[q];
     }
-    if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials + (size_t)tile_blocks(a.ntiles) * REDUCE_SLOTS);
+    if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
 
 // ---------------------------------------------------------- utility kernels
@@ -1610,9 +1693,15 @@ void launch_step_ax(const StepArgs &a, cudaStream_t s) {
     const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
     if constexpr (G && !WD && P != 0) {
         if (a.tiles) {  // the tile fluid kernel; inlet/outlet nodes and wall cells in launches of their own
-            if (a.ntiles > 0) k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
-            if constexpr (P == 2)  // FP16S fast tiles, two cells per thread
-                if (a.nfast > 0) k_step_pairs<AX><<<pair_blocks(a.nfast), STEP_THREADS, 0, s>>>(a);
+            if constexpr (P == 2) {
+                if (a.pairs) {  // FP16S: two cells per thread
+                    if (a.ntiles > 0) k_step_pairs<AX><<<pair_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
+                } else if (a.ntiles > 0) {
+                    k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
+                }
+            } else if (a.ntiles > 0) {
+                k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
+            }
             if (a.nwnodes > 0)
                 k_wall<P, G, WD, AX><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
             if (bb > 0) k_boundary<P, G, WD, AX><<<bb, STEP_THREADS, 0, s>>>(a);

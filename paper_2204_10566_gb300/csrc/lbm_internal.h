@@ -92,13 +92,11 @@ constexpr int ROW_RECORD_INTS = 12;
 constexpr int TILE_INTS = 12;
 constexpr uint32_t TILE_FAST = 1u << 31;
 
-// Group a chunk list (in row order) into tile records; mask: the link words,
-// n_row / periodic_row: the row axis (wrap-around copies at its ends).  The
-// records come in two runs, each in row order: the other tiles, then the
-// fast ones; *n_general receives the count of the first run.
+// Group a chunk list (in row order) into tile records, in the same order;
+// mask: the link words, n_row / periodic_row: the row axis (wrap-around
+// copies at its ends).
 std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
-                                 const std::vector<uint32_t> &mask, int n_row, bool periodic_row,
-                                 int64_t *n_general);
+                                 const std::vector<uint32_t> &mask, int n_row, bool periodic_row);
 
 // Flow parameters in the arithmetic precision of a kernel.
 template <class R>
@@ -141,9 +139,9 @@ struct alignas(16) StepArgs {
     const int4 *wnodes;        // cells with interpolated walls (x, row, slot, record), out of the chunk lanes
     int32_t nwnodes;
     int32_t wide_offsets;      // 1: 64-bit element offsets even when 32 bits would do (LBM_WIDE_OFFSETS=1)
-    const int32_t *tiles;      // tile records of the tile fluid kernel (NULL: chunk kernel)
-    int32_t ntiles;            // tiles the tile kernel updates (records 0 .. ntiles - 1)
-    int32_t nfast;             // FP16S fast tiles after them, for the pair kernel
+    const int32_t *tiles;      // tile records of the tile fluid kernels (NULL: chunk kernel)
+    int32_t ntiles;
+    int32_t pairs;             // 1: FP16S tiles on the pair kernel (two cells per thread)
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).
@@ -161,7 +159,7 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device);
 template <int P>
 int step_fluid_blocks(int32_t nchunks);
 // Blocks of the tile fluid kernel (one warp per tile) and of the FP16S pair
-// kernel (16 threads per fast tile).
+// kernel (16 threads per tile).
 __host__ __device__ inline int tile_blocks(int64_t ntiles) {
     return (int)((ntiles + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32));
 }
@@ -206,8 +204,7 @@ struct HostIndex {
     int32_t na_e = 0, nb_e = 0;           // extended extents of the two cross axes (row grid)
     std::vector<int32_t> row_nb;          // [rows][ROW_RECORD_INTS]
     std::vector<int2> chunks;             // chunk records (fluid cells)
-    std::vector<int32_t> tiles;           // [tiles][TILE_INTS] records of the tile fluid kernel
-    int64_t tiles_general = 0;            // records before the fast ones
+    std::vector<int32_t> tiles;           // [tiles][TILE_INTS] records of the tile fluid kernels
     std::vector<int4> bnodes;             // inlet/outlet nodes: x, row, slot, link word
     std::vector<uint32_t> mask;           // [nslots]
     std::vector<int32_t> slot_of_active;  // [n_active], active order = increasing box index

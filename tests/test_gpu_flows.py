@@ -278,9 +278,10 @@ def check_statistics(name, ref, runs, floor_run):
     of each region: within 2 % upstream of the expansion and in the near field
     of the jet, where the averages converge within the window; in the far
     field, where the jet breaks down and two realizations differ by more than
-    2 % over any affordable window, within the run-to-run variability: 1.5
-    times the difference between ref and floor_run (the same flow with another
-    inlet-noise seed) plus 1 %."""
+    2 % over any affordable window, within the run-to-run variability: twice
+    the difference between ref and floor_run (the same flow with another
+    inlet-noise seed) plus 1 % (the ratio of two such differences scatters
+    about 1)."""
     regions = statistics_regions(name)
     rel = lambda a, b, zs: float(np.linalg.norm(a[zs] - b[zs]) / np.linalg.norm(b[zs]))
     floor = rel(floor_run, ref, regions["far field"])
@@ -289,21 +290,21 @@ def check_statistics(name, ref, runs, floor_run):
         for region, zs in regions.items():
             e = rel(prof, ref, zs)
             report["%s %s" % (label, region)] = e
-            bound = 0.02 if region != "far field" else 1.5 * floor + 0.01
+            bound = 0.02 if region != "far field" else 2.0 * floor + 0.01
             assert e < bound, (label, region, e, bound)
     print(name, {k: round(v, 4) for k, v in report.items()})
     return report
 
 
 def test_transitional_nozzle_time_averaged_profiles(lbm):
-    """Re 3500 nozzle (96x96x800, parabolic inlet + 1 % noise), 20 000 steps
-    averaged over steps 10 001-20 000: FP32 and FP16-shifted <u_z> against the
+    """Re 3500 nozzle (96x96x800, parabolic inlet + 1 % noise), 30 000 steps
+    averaged over steps 10 001-30 000: FP32 and FP16-shifted <u_z> against the
     FP64 GPU run, region by region (check_statistics)."""
     name = "nozzle_re3500_96x96x800"
-    ref, n = nozzle_stats_run(lbm, name, "fp64", 20000, 10000)
-    assert n == 10000
-    floor = nozzle_stats_run(lbm, name, "fp32", 20000, 10000, seed=3)[0]
-    runs = {p: nozzle_stats_run(lbm, name, p, 20000, 10000)[0] for p in ("fp32", "fp16s")}
+    ref, n = nozzle_stats_run(lbm, name, "fp64", 30000, 10000)
+    assert n == 20000
+    floor = nozzle_stats_run(lbm, name, "fp32", 30000, 10000, seed=3)[0]
+    runs = {p: nozzle_stats_run(lbm, name, p, 30000, 10000)[0] for p in ("fp32", "fp16s")}
     check_statistics(name, ref, runs, floor)
 
 
