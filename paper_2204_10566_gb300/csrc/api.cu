@@ -39,10 +39,13 @@ struct lbm_ctx {
     int2 *d_chunks_wall = nullptr;   // chunk records without those cells (the fluid kernel's list)
     int32_t *d_tiles_wall = nullptr; // tile records without those cells
     int64_t n_tiles_wall = 0;
+    int2 *d_items_wall = nullptr;    // their pair-kernel items
+    int64_t n_items_wall = 0;
     bool wide_offsets = false;       // LBM_WIDE_OFFSETS=1 at creation: the 64-bit offset kernels always
     bool chunk_kernel = false;       // LBM_FLUID_KERNEL=chunk at creation: no tile fluid kernel
     bool pair_kernel = true;         // FP16S tiles two cells per thread (LBM_FLUID_KERNEL=tile: off)
     int32_t *d_tiles = nullptr;      // tile records of the tile fluid kernel
+    int2 *d_items = nullptr;         // work items of the FP16S pair kernel
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
@@ -129,6 +132,9 @@ void release_wall_q(lbm_ctx *c) {
     dev_free(c, c->d_wnodes, (size_t)c->n_wnodes * 16);
     if (c->d_chunks_wall) dev_free(c, c->d_chunks_wall, c->idx.chunks.size() * 8);
     if (c->d_tiles_wall) dev_free(c, c->d_tiles_wall, (size_t)c->n_tiles_wall * TILE_INTS * 4);
+    if (c->d_items_wall) dev_free(c, c->d_items_wall, (size_t)c->n_items_wall * 8);
+    c->d_items_wall = nullptr;
+    c->n_items_wall = 0;
     c->d_chunks_wall = nullptr;
     c->d_tiles_wall = nullptr;
     c->n_tiles_wall = 0;
@@ -149,7 +155,9 @@ void release_geometry(lbm_ctx *c) {
     dev_free(c, c->d_bnodes, c->idx.bnodes.size() * 16);
     dev_free(c, c->d_slot_of_active, c->idx.slot_of_active.size() * 4);
     dev_free(c, c->d_tiles, c->idx.tiles.size() * 4);
+    dev_free(c, c->d_items, c->idx.pair_items.size() * 8);
     c->d_tiles = nullptr;
+    c->d_items = nullptr;
     release_wall_q(c);
     dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     dev_free(c, c->d_health, 8 * 8);
@@ -214,11 +222,14 @@ int64_t tile_count(const lbm_ctx *c) {
 bool tiled(const lbm_ctx *c) {
     return c->desc.precision != LBM_FP64 && c->ghost1 && !wide_offsets(c) && !c->chunk_kernel && tile_count(c) > 0;
 }
-// FP16S tiles run on the pair kernel, FP32 tiles on the tile kernel.
+// FP16S tiles run on the pair kernel (over its work items), FP32 tiles on the tile kernel.
 bool pairs(const lbm_ctx *c) { return c->desc.precision == LBM_FP16S && c->pair_kernel; }
+int64_t item_count(const lbm_ctx *c) {
+    return c->d_tiles_wall ? c->n_items_wall : (int64_t)c->idx.pair_items.size();
+}
 int fluid_partials(const lbm_ctx *c) {
     if (!tiled(c)) return c->fluid_blocks;
-    return pairs(c) ? pair_blocks(tile_count(c)) : tile_blocks(tile_count(c));
+    return tile_blocks(pairs(c) ? item_count(c) : tile_count(c));
 }
 int step_partials(const lbm_ctx *c) {
     return fluid_partials(c) + node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(c->n_wnodes);
@@ -301,7 +312,10 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     if (tiled(c)) {
         a.tiles = c->d_tiles_wall ? c->d_tiles_wall : c->d_tiles;
         a.ntiles = (int32_t)tile_count(c);
-        a.pairs = pairs(c) ? 1 : 0;
+        if (pairs(c)) {
+            a.items = c->d_tiles_wall ? c->d_items_wall : c->d_items;
+            a.nitems = (int32_t)item_count(c);
+        }
     }
     const int key = (c->ghost1 ? 2 : 0) + (wide ? 1 : 0);
     if (c->prefetch_key != key) {
@@ -477,6 +491,7 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     const std::vector<int32_t> tiles =
         wn.empty() ? std::vector<int32_t>()
                    : build_tiles(chunks, c->idx.row_nb, c->idx.mask, c->idx.n_row, periodic_rows(c) != 0);
+    const std::vector<int2> items = build_pair_items(tiles);
     c->d_wall_qidx = (int32_t *)dev_alloc(c, qidx.size() * 4);
     c->d_wall_q = (uint8_t *)dev_alloc(c, rec.size());
     c->n_wall_q = n;
@@ -486,6 +501,8 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     if (!wn.empty()) {
         c->n_tiles_wall = (int64_t)tiles.size() / TILE_INTS;
         c->d_tiles_wall = (int32_t *)dev_alloc(c, tiles.size() * 4);
+        c->n_items_wall = (int64_t)items.size();
+        c->d_items_wall = (int2 *)dev_alloc(c, items.size() * 8);
     }
     const int capacity = partial_capacity(c, c->n_wnodes);
     double *partials = c->d_partials;
@@ -497,8 +514,8 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
             c->nblocks = capacity;
         }
     }
-    if (!c->d_wall_qidx || !c->d_wall_q || (!wn.empty() && (!c->d_wnodes || !c->d_chunks_wall || !c->d_tiles_wall)) ||
-        !partials) {
+    if (!c->d_wall_qidx || !c->d_wall_q ||
+        (!wn.empty() && (!c->d_wnodes || !c->d_chunks_wall || !c->d_tiles_wall || !c->d_items_wall)) || !partials) {
         release_wall_q(c);
         return fail(c, LBM_ERR_OOM, "wall-distance allocation failed");
     }
@@ -514,6 +531,9 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     if (!tiles.empty())
         CK(cudaMemcpyAsync(c->d_tiles_wall, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, c->stream),
            "copy tile records");
+    if (!items.empty())
+        CK(cudaMemcpyAsync(c->d_items_wall, items.data(), items.size() * 8, cudaMemcpyHostToDevice, c->stream),
+           "copy pair items");
     CK(cudaStreamSynchronize(c->stream), "sync wall distances");
     return LBM_OK;
 }
@@ -540,6 +560,7 @@ int64_t ctx_footprint(const lbm_desc &d, const HostIndex &ix) {
                                              node_blocks(ix.n_active));
     return 2 * pop + (ix.nslots + 2 * MASK_MARGIN) * 4 + (int64_t)ix.row_nb.size() * 4 + (int64_t)ix.chunks.size() * 8 +
            (int64_t)ix.bnodes.size() * 16 + ix.n_active * 4 + (int64_t)ix.tiles.size() * 4 +
+           (int64_t)ix.pair_items.size() * 8 +
            blocks * REDUCE_SLOTS * 8 + 64 + 256;
 }
 
@@ -562,11 +583,12 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
     c->d_bnodes = (int4 *)dev_alloc(c, c->idx.bnodes.size() * 16);
     c->d_slot_of_active = (int32_t *)dev_alloc(c, c->idx.slot_of_active.size() * 4);
     c->d_tiles = (int32_t *)dev_alloc(c, c->idx.tiles.size() * 4);
+    c->d_items = (int2 *)dev_alloc(c, c->idx.pair_items.size() * 8);
     c->d_partials = (double *)dev_alloc(c, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     c->d_health = (double *)dev_alloc(c, 8 * 8);
     c->d_status = (uint32_t *)dev_alloc(c, 256);
     if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_nb || !c->d_chunks || !c->d_bnodes || !c->d_slot_of_active ||
-        !c->d_tiles || !c->d_partials || !c->d_health || !c->d_status) {
+        !c->d_tiles || !c->d_items || !c->d_partials || !c->d_health || !c->d_status) {
         release_geometry(c);
         return fail(c, LBM_ERR_OOM, "device allocation failed in lbm_set_geometry");
     }
@@ -589,6 +611,10 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
         CK(cudaMemcpyAsync(c->d_tiles, c->idx.tiles.data(), c->idx.tiles.size() * 4, cudaMemcpyHostToDevice,
                            c->stream),
            "copy tile records");
+    if (!c->idx.pair_items.empty())
+        CK(cudaMemcpyAsync(c->d_items, c->idx.pair_items.data(), c->idx.pair_items.size() * 8,
+                           cudaMemcpyHostToDevice, c->stream),
+           "copy pair items");
     // Padding slots are never read by the step kernel; zero both buffers so
     // that checkpoints and dumps are deterministic.
     CK(cudaMemsetAsync(c->f_raw[0], 0, raw_pop_bytes(c), c->stream), "clear f0");

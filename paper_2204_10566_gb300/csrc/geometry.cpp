@@ -269,7 +269,24 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
         }
     if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
     out.tiles = build_tiles(out.chunks, out.row_nb, out.mask, F.np, F.pp);
+    out.pair_items = build_pair_items(out.tiles);
     return "";
+}
+
+std::vector<int2> build_pair_items(const std::vector<int32_t> &tiles) {
+    const int64_t nt = (int64_t)tiles.size() / TILE_INTS;
+    auto fast = [&](int64_t t) { return ((uint32_t)tiles[(size_t)t * TILE_INTS] & TILE_FAST) != 0u; };
+    std::vector<int2> items;
+    for (int64_t t = 0; t < nt;) {
+        if (fast(t) && t + 1 < nt && fast(t + 1)) {
+            items.push_back(make_int2((int)t, (int)t + 1));
+            t += 2;
+        } else {
+            items.push_back(make_int2((int)t, -1));
+            t += 1;
+        }
+    }
+    return items;
 }
 
 std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
@@ -476,6 +493,19 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     }
     for (int64_t b = 0; b < (int64_t)in_tile.size(); ++b)
         if ((flags[b] == LBM_FLUID) != (in_tile[b] == 1)) return "fluid cell not in exactly one tile lane";
+    // pair-kernel items: every tile exactly once; both tiles of a pair fast
+    std::vector<uint8_t> in_item((size_t)nt, 0);
+    for (const int2 &it : ix.pair_items) {
+        if (it.x < 0 || it.x >= nt || in_item[(size_t)it.x]++) return "pair item tile";
+        if (it.y >= 0) {
+            if (it.y >= nt || in_item[(size_t)it.y]++) return "pair item tile";
+            if (!((uint32_t)ix.tiles[(size_t)it.x * TILE_INTS] & TILE_FAST) ||
+                !((uint32_t)ix.tiles[(size_t)it.y * TILE_INTS] & TILE_FAST))
+                return "pair item of a tile that is not fast";
+        }
+    }
+    for (int64_t t = 0; t < nt; ++t)
+        if (in_item[(size_t)t] != 1) return "tile not in exactly one pair item";
 
     return "";
 }

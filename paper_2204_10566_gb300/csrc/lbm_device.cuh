@@ -1263,74 +1263,79 @@ struct SharedStore {
     }
 };
 
+// One warp's update of tile t (lane = the warp lane, out = the warp's
+// shared-memory slice of TileOut<P>::ELEMS elements).
 template <int P, int AX>
-__global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step_tiles(const StepArgs a) {
+__device__ __forceinline__ void tile_update(const StepArgs &a, int t, int lane, typename TileOut<P>::T *out,
+                                            double (&hv)[6]) {
     using O = TileOut<P>;
     using T = typename O::T;
     using R = typename Storage<P>::R;
     constexpr bool RAW = Storage<P>::SCALED;
-    __shared__ __align__(16) T staged_out[STEP_THREADS / 32][O::ELEMS];
+    const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * (size_t)t;
+    const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+    const int nb[9] = {r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+    const bool fast = ((uint32_t)r0.x & TILE_FAST) != 0u;
+    const int p0 = (int)((uint32_t)r0.x & CHUNK_X0_MASK);
+    const int x = p0 + lane, slot = nb[4] + x;
+    const bool fluid = ((uint32_t)r0.y >> lane) & 1u;
+    R d[27];
+    gather<P, false, AX, RAW>(a, nb, x, d);  // every lane's pulls lie inside the buffer margins
+    R rho, ux, uy, uz;
+    if (fast) {
+        const SharedStore<P, RAW> sink{a, slot, out + lane};
+        collide_ghost1<R, RAW, SharedStore<P, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
+                                                    R(a.scale), &sink);
+        __syncwarp();
+        // piece q = 4 i + k (FP16S) / 8 i + k (FP32): elements 16k/S.. of population i,
+        // at shared offset 16 q bytes and at own slots nb[4] + p0 + k PIECE
+        T *fout = static_cast<T *>(a.fout) + (nb[4] + p0);
+#pragma unroll
+        for (int q0 = 0; q0 < 27 * O::PIECES; q0 += 32) {
+            const int q = q0 + lane;
+            if (q < 27 * O::PIECES) {
+                const int4 v = reinterpret_cast<const int4 *>(out)[q];
+                const int i = q / O::PIECES, k = q % O::PIECES;
+                *reinterpret_cast<int4 *>(fout + elem<false>(i, a.stride, k * O::PIECE)) = v;
+            }
+        }
+        __syncwarp();
+    } else {
+        const bool present = ((uint32_t)r0.z >> lane) & 1u;
+        const uint32_t m = present ? __ldg(a.mask + slot) : 0u;
+        const uint32_t links = fluid ? (m & LINK_MASK) : 0u;
+        const uint32_t own = fluid ? (LINK_MASK | OWN_FLUID)
+                                   : (present && ((m >> TYPE_SHIFT) & 3u) == TYPE_PAD ? (~m & LINK_MASK) : 0u);
+        const LineStore<P, false, RAW, AX> sink{a, nb, x, slot, links, own};
+        collide_ghost1<R, RAW, LineStore<P, false, RAW, AX>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
+                                                             R(a.scale), &sink);
+    }
+    if (fluid) record_cell(a, slot, rho, ux, uy, uz, hv);
+}
+
+template <int P, int AX>
+__global__ void __launch_bounds__(STEP_THREADS, LBM_STEP_MIN_BLOCKS) k_step_tiles(const StepArgs a) {
+    using O = TileOut<P>;
+    __shared__ __align__(16) typename O::T staged_out[STEP_THREADS / 32][O::ELEMS];
     const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
     const int t = (int)blockIdx.x * (STEP_THREADS / 32) + warp;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (t < a.ntiles) {  // uniform over the warp
-        const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * (size_t)t;
-        const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
-        const int nb[9] = {r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
-        const bool fast = ((uint32_t)r0.x & TILE_FAST) != 0u;
-        const int p0 = (int)((uint32_t)r0.x & CHUNK_X0_MASK);
-        const int x = p0 + lane, slot = nb[4] + x;
-        const bool fluid = ((uint32_t)r0.y >> lane) & 1u;
-        R d[27];
-        gather<P, false, AX, RAW>(a, nb, x, d);  // every lane's pulls lie inside the buffer margins
-        R rho, ux, uy, uz;
-        if (fast) {
-            T *out = staged_out[warp];
-            const SharedStore<P, RAW> sink{a, slot, out + lane};
-            collide_ghost1<R, RAW, SharedStore<P, RAW>>(d, flow<R>(a).omega, rho, ux, uy, uz, R(a.inv_scale),
-                                                        R(a.scale), &sink);
-            __syncwarp();
-            // piece q = 4 i + k (FP16S) / 8 i + k (FP32): elements 16k/S.. of population i,
-            // at shared offset 16 q bytes and at own slots nb[4] + p0 + k PIECE
-            T *fout = static_cast<T *>(a.fout) + (nb[4] + p0);
-#pragma unroll
-            for (int q0 = 0; q0 < 27 * O::PIECES; q0 += 32) {
-                const int q = q0 + lane;
-                if (q < 27 * O::PIECES) {
-                    const int4 v = reinterpret_cast<const int4 *>(out)[q];
-                    const int i = q / O::PIECES, k = q % O::PIECES;
-                    *reinterpret_cast<int4 *>(fout + elem<false>(i, a.stride, k * O::PIECE)) = v;
-                }
-            }
-            __syncwarp();
-        } else {
-            const bool present = ((uint32_t)r0.z >> lane) & 1u;
-            const uint32_t m = present ? __ldg(a.mask + slot) : 0u;
-            const uint32_t links = fluid ? (m & LINK_MASK) : 0u;
-            const uint32_t own = fluid ? (LINK_MASK | OWN_FLUID)
-                                       : (present && ((m >> TYPE_SHIFT) & 3u) == TYPE_PAD ? (~m & LINK_MASK) : 0u);
-            const LineStore<P, false, RAW, AX> sink{a, nb, x, slot, links, own};
-            collide_ghost1<R, RAW, LineStore<P, false, RAW, AX>>(d, flow<R>(a).omega, rho, ux, uy, uz,
-                                                                 R(a.inv_scale), R(a.scale), &sink);
-        }
-        if (fluid) record_cell(a, slot, rho, ux, uy, uz, hv);
-    }
+    if (t < a.ntiles) tile_update<P, AX>(a, t, lane, staged_out[warp], hv);  // uniform over the warp
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
 
 // ------------------------------------------------ pair fluid kernel (FP16S)
 //
-// The tiles of an FP16S lattice with two adjacent cells per thread: 16
-// threads per tile, thread k updates cells x = p0 + 2k and x + 1.  The
-// collision runs on the packed FP32 pipe across the pair (one instruction
-// for both cells); its 27 inputs stay FP16 pairs until the moment pass
-// converts them; the pull of each line along the row (c = 0 along the row
-// axis) is one aligned 32-bit load of both cells' values, the other two are
-// two 16-bit loads.  A fast tile (32 fluid cells, no wall link, no
-// wrap-around copy) writes each output as one 32-bit store of both cells'
-// own slots; other tiles go through a per-cell line sink (PairLineStore).
-// Every thread holds two cells, so the kernel runs at fewer resident warps
-// than the one-cell kernels with the same bytes in flight per SM.
+// Fast tiles of an FP16S lattice (32 fluid cells, no wall link, no
+// wrap-around copy) with two adjacent cells per thread: 16 threads per
+// tile, thread k updates cells x = p0 + 2k and x + 1.  The collision runs on
+// the packed FP32 pipe across the pair (one instruction for both cells); its
+// 27 inputs stay FP16 pairs until the moment pass converts them; the pull
+// of each line along the row (c = 0 along the row axis) is one aligned
+// 32-bit load of both cells' values, the other two are two 16-bit loads;
+// each output is one 32-bit store of both cells' own slots.  Every thread
+// holds two cells, so the kernel runs at fewer resident warps than the
+// one-cell kernels with the same bytes in flight per SM.
 #ifndef LBM_PAIR_MIN_BLOCKS
 #define LBM_PAIR_MIN_BLOCKS 5
 #endif
@@ -1357,15 +1362,14 @@ __device__ __forceinline__ void gather_pair(const StepArgs &a, const int (&nb)[9
     }
 }
 
-// Viscous stress of the pair's fluid cells (statistics sample steps).
-__device__ __forceinline__ void record_stress_pair(const StepArgs &a, int slot, F2 omega, const F2 (&a2)[6],
-                                                   bool fluid0, bool fluid1) {
+// Viscous stress of the pair's two cells (statistics sample steps).
+__device__ __forceinline__ void record_stress_pair(const StepArgs &a, int slot, F2 omega, const F2 (&a2)[6]) {
     if ((a.flags & (STEP_STATS | STEP_STATS_FULL)) != (STEP_STATS | STEP_STATS_FULL)) return;
     float ax[6], ay[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) ax[q] = a2[q].v.x, ay[q] = a2[q].v.y;
-    if (fluid0) record_stress(a, slot, omega.v.x, ax);
-    if (fluid1) record_stress(a, slot + 1, omega.v.y, ay);
+    record_stress(a, slot, omega.v.x, ax);
+    record_stress(a, slot + 1, omega.v.y, ay);
 }
 
 // Output sink of a fast tile: both cells' values of population i as one FP16
@@ -1374,7 +1378,7 @@ struct PairStore {
     const StepArgs &a;
     int slot;
     __device__ __forceinline__ void moments(F2 omega, const F2 (&a2)[6]) const {
-        record_stress_pair(a, slot, omega, a2, true, true);
+        record_stress_pair(a, slot, omega, a2);
     }
     __device__ __forceinline__ void operator()(int j, F2 vm, F2 v0, F2 vp) const {
         const uint32_t st = (uint32_t)a.stride;
@@ -1385,103 +1389,44 @@ struct PairStore {
     }
 };
 
-// Output sink of the other tiles: LineStore's stores for each cell of the
-// pair (own slots by the own masks, one 32-bit store when both cells take
-// population i; ghost slots of each cell's wall links; wrap-around copies).
+// Half a warp's update of fast tile t with two cells per thread (k: the
+// pair within the tile).
 template <int AX>
-struct PairLineStore {
-    const StepArgs &a;
-    const int (&nb)[9];
-    int x, slot;
-    uint32_t links0, links1, own0, own1;
-    __device__ __forceinline__ void put(int i, int s, float v) const {
-        static_cast<__half *>(a.fout)[elem<false>(i, a.stride, s)] = __float2half_rn(v);
-    }
-    __device__ __forceinline__ void moments(F2 omega, const F2 (&a2)[6]) const {
-        record_stress_pair(a, slot, omega, a2, (own0 & OWN_FLUID) != 0u, (own1 & OWN_FLUID) != 0u);
-    }
-    __device__ __forceinline__ void operator()(int j, F2 vm, F2 v0, F2 vp) const {
-        const F2 v[3] = {vm, v0, vp};
+__device__ __forceinline__ void pair_update(const StepArgs &a, int t, int k, double (&hv)[6]) {
+    const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * (size_t)t;
+    const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+    const int nb[9] = {r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+    const int x = (int)((uint32_t)r0.x & CHUNK_X0_MASK) + 2 * k, slot = nb[4] + x;
+    __half2 d[27];
+    gather_pair<AX>(a, nb, x, d);
+    F2 m[10], rho, ux, uy, uz;
+    ghost1_sums(d, Half2ToF2{}, m);
+    ghost1_finish<F2, true>(m, F2(a.pf.omega), rho, ux, uy, uz, F2(a.inv_scale), F2(a.scale), PairStore{a, slot});
+    double h0[6] = {0, 0, 0, 0, 0, 0}, h1[6] = {0, 0, 0, 0, 0, 0};
+    record_cell(a, slot, rho.v.x, ux.v.x, uy.v.x, uz.v.x, h0);
+    record_cell(a, slot + 1, rho.v.y, ux.v.y, uy.v.y, uz.v.y, h1);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int i = 3 * j + c;
-            const bool b0 = (own0 >> i) & 1u, b1 = (own1 >> i) & 1u;
-            if (b0 && b1) {
-                *reinterpret_cast<__half2 *>(static_cast<__half *>(a.fout) + elem<false>(i, a.stride, slot)) =
-                    __float22half2_rn(v[c].v);
-            } else {
-                if (b0) put(i, slot, v[c].v.x);
-                if (b1) put(i, slot + 1, v[c].v.y);
-            }
-        }
-        const int jl = 8 - j;  // links 26 - i of this line's values sit in line 8 - j
-        if ((links0 | links1) & (7u << (3 * jl))) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int k = 26 - (3 * j + c);  // wall link k takes value 3j + c
-                const int s = nb[row_line<AX>(k)] + x - c_row<AX>(k);
-                if (links0 & (1u << k)) put(k, s, v[c].v.x);
-                if (links1 & (1u << k)) put(k, s + 1, v[c].v.y);
-            }
-        }
-        if (a.periodic_row) {  // wrap-around copies across the periodic row faces
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int i = 3 * j + c;
-                if (c_row<AX>(i) == 1) {
-                    if ((own0 & OWN_FLUID) && x == a.n_row - 1) put(i, nb[4] - 1, v[c].v.x);
-                    if ((own1 & OWN_FLUID) && x + 1 == a.n_row - 1) put(i, nb[4] - 1, v[c].v.y);
-                }
-                if (c_row<AX>(i) == -1) {
-                    if ((own0 & OWN_FLUID) && x == 0) put(i, nb[4] + a.n_row, v[c].v.x);
-                }
-            }
-        }
-    }
-};
-
-// Own-slot mask of a cell for LineStore-style sinks: every population for a
-// fluid cell; for a padding or ghost slot of the tile, the populations that
-// nobody reads there (filler that completes the row-end sectors); nothing
-// for inlet/outlet slots and lanes outside the tile's chunks.
-__device__ __forceinline__ uint32_t own_mask(bool fluid, bool present, uint32_t m) {
-    return fluid ? (LINK_MASK | OWN_FLUID) : (present && ((m >> TYPE_SHIFT) & 3u) == TYPE_PAD ? (~m & LINK_MASK) : 0u);
+    for (int q = 0; q < 6; ++q) hv[q] = q == 4 ? fmax(h0[q], h1[q]) : h0[q] + h1[q];
 }
 
+// FP16S fluid kernel over work items, one per warp: an item of two fast
+// tiles runs on the pair path (16 threads per tile, two cells per thread); an
+// item of one tile (a tile with walls, or a fast tile without a fast
+// neighbour in the row order) runs on the one-cell tile path.  Items follow
+// the tiles' row order, and the branch is uniform over the warp.
 template <int AX>
 __global__ void __launch_bounds__(STEP_THREADS, LBM_PAIR_MIN_BLOCKS) k_step_pairs(const StepArgs a) {
-    const int g = (int)(blockIdx.x * STEP_THREADS + threadIdx.x);
-    const int t = g >> 4, k = g & 15;  // tile, pair within it
+    using O = TileOut<2>;
+    __shared__ __align__(16) typename O::T staged_out[STEP_THREADS / 32][O::ELEMS];
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    const int w = (int)blockIdx.x * (STEP_THREADS / 32) + warp;
     double hv[6] = {0, 0, 0, 0, 0, 0};
-    if (t < a.ntiles) {  // uniform over the 16 threads of the tile
-        const int4 *rec = reinterpret_cast<const int4 *>(a.tiles) + 3 * (size_t)t;
-        const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
-        const int nb[9] = {r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
-        const bool fast = ((uint32_t)r0.x & TILE_FAST) != 0u;
-        const int x = (int)((uint32_t)r0.x & CHUNK_X0_MASK) + 2 * k, slot = nb[4] + x;
-        const bool fluid0 = ((uint32_t)r0.y >> (2 * k)) & 1u, fluid1 = ((uint32_t)r0.y >> (2 * k + 1)) & 1u;
-        __half2 d[27];
-        gather_pair<AX>(a, nb, x, d);  // every lane's pulls lie inside the buffer margins
-        F2 m[10], rho, ux, uy, uz;
-        ghost1_sums(d, Half2ToF2{}, m);
-        const F2 omega(a.pf.omega), in_s(a.inv_scale), out_s(a.scale);
-        if (fast) {
-            ghost1_finish<F2, true>(m, omega, rho, ux, uy, uz, in_s, out_s, PairStore{a, slot});
-        } else {
-            const bool present0 = ((uint32_t)r0.z >> (2 * k)) & 1u, present1 = ((uint32_t)r0.z >> (2 * k + 1)) & 1u;
-            const uint2 mm = present0 || present1 ? __ldg(reinterpret_cast<const uint2 *>(a.mask + slot))
-                                                  : make_uint2(0u, 0u);
-            const uint32_t m0 = present0 ? mm.x : 0u, m1 = present1 ? mm.y : 0u;
-            const PairLineStore<AX> sink{a, nb, x, slot, fluid0 ? (m0 & LINK_MASK) : 0u,
-                                         fluid1 ? (m1 & LINK_MASK) : 0u, own_mask(fluid0, present0, m0),
-                                         own_mask(fluid1, present1, m1)};
-            ghost1_finish<F2, true>(m, omega, rho, ux, uy, uz, in_s, out_s, sink);
-        }
-        double h0[6] = {0, 0, 0, 0, 0, 0}, h1[6] = {0, 0, 0, 0, 0, 0};
-        if (fluid0) record_cell(a, slot, rho.v.x, ux.v.x, uy.v.x, uz.v.x, h0);
-        if (fluid1) record_cell(a, slot + 1, rho.v.y, ux.v.y, uy.v.y, uz.v.y, h1);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) hv[q] = q == 4 ? fmax(h0[q], h1[q]) : h0[q] + h1[q];
+    if (w < a.nitems) {
+        const int2 item = __ldg(a.items + w);
+        if (item.y >= 0)
+            pair_update<AX>(a, lane < 16 ? item.x : item.y, lane & 15, hv);
+        else
+            tile_update<2, AX>(a, item.x, lane, staged_out[warp], hv);
     }
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
@@ -1694,8 +1639,8 @@ void launch_step_ax(const StepArgs &a, cudaStream_t s) {
     if constexpr (G && !WD && P != 0) {
         if (a.tiles) {  // the tile fluid kernel; inlet/outlet nodes and wall cells in launches of their own
             if constexpr (P == 2) {
-                if (a.pairs) {  // FP16S: two cells per thread
-                    if (a.ntiles > 0) k_step_pairs<AX><<<pair_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
+                if (a.items) {  // FP16S: pairs of fast tiles two cells per thread
+                    if (a.nitems > 0) k_step_pairs<AX><<<tile_blocks(a.nitems), STEP_THREADS, 0, s>>>(a);
                 } else if (a.ntiles > 0) {
                     k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
                 }

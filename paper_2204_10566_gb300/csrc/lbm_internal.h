@@ -97,6 +97,9 @@ constexpr uint32_t TILE_FAST = 1u << 31;
 // copies at its ends).
 std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
                                  const std::vector<uint32_t> &mask, int n_row, bool periodic_row);
+// Work items of the FP16S pair kernel over tile records in row order: (t, t + 1)
+// for two consecutive fast tiles, (t, -1) for any other tile.
+std::vector<int2> build_pair_items(const std::vector<int32_t> &tiles);
 
 // Flow parameters in the arithmetic precision of a kernel.
 template <class R>
@@ -141,7 +144,8 @@ struct alignas(16) StepArgs {
     int32_t wide_offsets;      // 1: 64-bit element offsets even when 32 bits would do (LBM_WIDE_OFFSETS=1)
     const int32_t *tiles;      // tile records of the tile fluid kernels (NULL: chunk kernel)
     int32_t ntiles;
-    int32_t pairs;             // 1: FP16S tiles on the pair kernel (two cells per thread)
+    const int2 *items;         // FP16S work items of the pair kernel (NULL: tile kernel)
+    int32_t nitems;
 };
 
 // Launchers, one set per storage precision (P = 0 FP64, 1 FP32, 2 FP16S).
@@ -158,8 +162,8 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device);
 // Blocks of one step's fluid kernel (partial-sum slots it writes).
 template <int P>
 int step_fluid_blocks(int32_t nchunks);
-// Blocks of the tile fluid kernel (one warp per tile) and of the FP16S pair
-// kernel (16 threads per tile).
+// Blocks of the tile fluid kernel (one warp per tile or per pair-kernel item)
+// and of a grid with 16 threads per tile.
 __host__ __device__ inline int tile_blocks(int64_t ntiles) {
     return (int)((ntiles + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32));
 }
@@ -205,6 +209,7 @@ struct HostIndex {
     std::vector<int32_t> row_nb;          // [rows][ROW_RECORD_INTS]
     std::vector<int2> chunks;             // chunk records (fluid cells)
     std::vector<int32_t> tiles;           // [tiles][TILE_INTS] records of the tile fluid kernels
+    std::vector<int2> pair_items;         // work items of the FP16S pair kernel
     std::vector<int4> bnodes;             // inlet/outlet nodes: x, row, slot, link word
     std::vector<uint32_t> mask;           // [nslots]
     std::vector<int32_t> slot_of_active;  // [n_active], active order = increasing box index

@@ -3,8 +3,9 @@
 With the default ghost rates and 32-bit offsets, FP32 and FP16S lattices run
 the tile fluid kernel (one warp per tile of up to 32 consecutive cells of a
 row; tiles of 32 fluid cells without wall links store through shared
-memory), and FP16S runs those fast tiles on the pair kernel (two adjacent
-cells per thread on the packed FP32 pipe).  LBM_FLUID_KERNEL, read when a
+memory), and FP16S runs pairs of consecutive such tiles on the pair kernel
+(two adjacent cells per thread on the packed FP32 pipe), every other tile on
+the one-cell tile path of the same launch.  LBM_FLUID_KERNEL, read when a
 context is created, selects "tile" (no pair kernel) or "chunk" (the chunk
 kernel) instead.  Both must meet the
 method's tolerances on geometries that exercise every path: walls in every
