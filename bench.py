@@ -119,18 +119,6 @@ def recorded_traffic(workload, precision):
     return None
 
 
-def launches_per_step(flags, periodic, precision="fp32"):
-    """Kernels one lattice step launches: the fluid kernel, whose trailing
-    blocks update the inlet/outlet nodes in FP32; in FP16S and FP64 the
-    inlet/outlet kernel is a launch of its own when the geometry has such
-    nodes."""
-    from paper_2204_10566_gb300 import lbm
-
-    if precision == "fp32":
-        return 1
-    return 1 + (1 if lbm.check_layout(flags, periodic)["boundary_nodes"] > 0 else 0)
-
-
 class ClockSampler:
     """nvidia-smi SM clock / throttle-reason samples during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -258,13 +246,16 @@ def time_precision(lbm, torch, flags, params, periodic, precision, steps, warmup
     G.step(warmup).sync()
     if sampler:
         sampler.start()
+    launched0 = G.kernel_launches()
     times = timed_regions(torch, G.stream, lambda: G.step(steps), steps, min_seconds, dist, device)
     clocks = sampler.stop() if sampler else None
     G.sync()
     info = G.layout_info()
+    launched = G.kernel_launches() - launched0
     G.close()
     timing = {"regions": len(times), "steps_per_region": steps, "stat": "median",
-              "ms_region_min": min(times), "ms_region_max": max(times)}
+              "ms_region_min": min(times), "ms_region_max": max(times),
+              "launches_per_region": round(launched / (len(times) + 1))}  # the probe region and the timed ones
     return n, statistics.median(times), clocks, info, timing
 
 
@@ -564,7 +555,7 @@ def ours_arm(args):
         "by_precision": by_prec,
         "by_walls": by_walls,
         "e2e": e2e,
-        "gpu_launches": args.steps * launches_per_step(flags, periodic, head),
+        "gpu_launches": timing["launches_per_region"],
         "timing": dict(timing, note="gpu_launches counts the kernels of one timed K-step region"),
         "clocks": clocks,
         "cpu_baseline": cpu,

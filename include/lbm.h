@@ -363,6 +363,15 @@ lbm_status lbm_totals_noalloc(const void *f, int32_t precision, float fp16_scale
  * row padding), bytes of one population buffer, device bytes held. */
 lbm_status lbm_layout_info(lbm_ctx *ctx, int64_t *slots, int64_t *buffer_bytes, int64_t *device_bytes);
 
+/* Kernels lbm_step has launched on this context since its creation, counted
+ * at each launch: the fluid kernel(s) of the variant that runs (FP32: the
+ * tile kernel; FP16S: the chunk kernel and the pair kernel; FP64 and general
+ * ghost rates: the chunk kernel), the interpolated-wall kernel, the
+ * inlet/outlet kernel and, on health-check steps, the final reduction pass.
+ * The difference of two readings is the launch count of the steps between
+ * them.  LBM_ERR_ARG if ctx or n is NULL. */
+lbm_status lbm_kernel_launches(lbm_ctx *ctx, int64_t *n);
+
 /* ------------------------------------------------------------------ serving
  * A request server runs many lattices (nozzle / pipe runs of different
  * sizes, Re, step counts and storage precisions) on one GPU with continuous

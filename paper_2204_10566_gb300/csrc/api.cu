@@ -41,11 +41,14 @@ struct lbm_ctx {
     int64_t n_tiles_wall = 0;
     int2 *d_items_wall = nullptr;    // their pair-kernel items
     int64_t n_items_wall = 0;
+    int2 *d_rest_wall = nullptr;     // and the chunks beside those items
+    int64_t n_rest_wall = 0;
     bool wide_offsets = false;       // LBM_WIDE_OFFSETS=1 at creation: the 64-bit offset kernels always
-    bool chunk_kernel = false;       // LBM_FLUID_KERNEL=chunk at creation: no tile fluid kernel
-    bool pair_kernel = true;         // FP16S tiles two cells per thread (LBM_FLUID_KERNEL=tile: off)
+    FluidKernel fluid_kernel = FluidKernel::AUTO;  // LBM_FLUID_KERNEL at creation
+    SideStream side;                 // the wall-cell and inlet/outlet kernels beside the fluid kernel
     int32_t *d_tiles = nullptr;      // tile records of the tile fluid kernel
-    int2 *d_items = nullptr;         // work items of the FP16S pair kernel
+    int2 *d_items = nullptr;         // pairs of fast tiles of the FP16S pair kernel
+    int2 *d_rest = nullptr;          // chunks of the other tiles (the chunk kernel beside it)
     double *d_partials = nullptr;
     double *d_health = nullptr;
     uint32_t *d_status = nullptr;
@@ -53,6 +56,7 @@ struct lbm_ctx {
     int nblocks = 0;        // partial-sum capacity (blocks)
     int fluid_blocks = 0;   // blocks of the chunk fluid kernel
     int64_t device_bytes = 0;
+    int64_t kernel_launches = 0;  // kernels lbm_step has launched on this context
     // parameters and state
     lbm_params params{};
     double omega = 0.0;
@@ -133,8 +137,11 @@ void release_wall_q(lbm_ctx *c) {
     if (c->d_chunks_wall) dev_free(c, c->d_chunks_wall, c->idx.chunks.size() * 8);
     if (c->d_tiles_wall) dev_free(c, c->d_tiles_wall, (size_t)c->n_tiles_wall * TILE_INTS * 4);
     if (c->d_items_wall) dev_free(c, c->d_items_wall, (size_t)c->n_items_wall * 8);
+    if (c->d_rest_wall) dev_free(c, c->d_rest_wall, (size_t)c->n_rest_wall * 8);
     c->d_items_wall = nullptr;
     c->n_items_wall = 0;
+    c->d_rest_wall = nullptr;
+    c->n_rest_wall = 0;
     c->d_chunks_wall = nullptr;
     c->d_tiles_wall = nullptr;
     c->n_tiles_wall = 0;
@@ -156,8 +163,10 @@ void release_geometry(lbm_ctx *c) {
     dev_free(c, c->d_slot_of_active, c->idx.slot_of_active.size() * 4);
     dev_free(c, c->d_tiles, c->idx.tiles.size() * 4);
     dev_free(c, c->d_items, c->idx.pair_items.size() * 8);
+    dev_free(c, c->d_rest, c->idx.rest_chunks.size() * 8);
     c->d_tiles = nullptr;
     c->d_items = nullptr;
+    c->d_rest = nullptr;
     release_wall_q(c);
     dev_free(c, c->d_partials, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     dev_free(c, c->d_health, 8 * 8);
@@ -211,25 +220,34 @@ int periodic_rows(const lbm_ctx *c) {
     return (c->desc.periodic & (c->idx.row_axis == 2 ? LBM_PERIODIC_Z : LBM_PERIODIC_X)) ? 1 : 0;
 }
 
-// Whether the next steps run the tile fluid kernel (FP32 / FP16S, default
-// ghost rates, 32-bit offsets), and the partial sums the step kernels write:
-// the fluid kernel's blocks, then the inlet/outlet blocks, then the wall-cell
+// Whether the next steps run the tile fluid kernel (default ghost rates,
+// 32-bit offsets; FP32 by default, FP16S when LBM_FLUID_KERNEL asks for the
+// tile or the pair kernel), and the partial sums the step kernels write: the
+// fluid kernel's blocks, then the inlet/outlet blocks, then the wall-cell
 // blocks.
 bool wide_offsets(const lbm_ctx *c) { return c->wide_offsets || c->idx.nslots > MAX_SLOTS_32; }
 int64_t tile_count(const lbm_ctx *c) {
     return c->d_tiles_wall ? c->n_tiles_wall : (int64_t)c->idx.tiles.size() / TILE_INTS;
 }
 bool tiled(const lbm_ctx *c) {
-    return c->desc.precision != LBM_FP64 && c->ghost1 && !wide_offsets(c) && !c->chunk_kernel && tile_count(c) > 0;
+    const FluidKernel k = c->fluid_kernel;
+    const bool wanted = k == FluidKernel::TILE || k == FluidKernel::PAIRS ||
+                        (k == FluidKernel::AUTO && c->desc.precision == LBM_FP32);
+    return wanted && c->desc.precision != LBM_FP64 && c->ghost1 && !wide_offsets(c) && tile_count(c) > 0;
 }
-// FP16S tiles run on the pair kernel (over its work items), FP32 tiles on the tile kernel.
-bool pairs(const lbm_ctx *c) { return c->desc.precision == LBM_FP16S && c->pair_kernel; }
+// LBM_FLUID_KERNEL=pairs splits the FP16S fluid cells: pairs of fast tiles
+// run on the pair kernel, the chunks of every other tile on the chunk kernel.
+bool pairs(const lbm_ctx *c) { return c->desc.precision == LBM_FP16S && c->fluid_kernel == FluidKernel::PAIRS; }
 int64_t item_count(const lbm_ctx *c) {
     return c->d_tiles_wall ? c->n_items_wall : (int64_t)c->idx.pair_items.size();
 }
+int64_t rest_count(const lbm_ctx *c) {
+    return c->d_tiles_wall ? c->n_rest_wall : (int64_t)c->idx.rest_chunks.size();
+}
+int split_blocks(int64_t rest, int64_t items) { return fluid_blocks((int32_t)rest) + tile_blocks(items); }
 int fluid_partials(const lbm_ctx *c) {
     if (!tiled(c)) return c->fluid_blocks;
-    return tile_blocks(pairs(c) ? item_count(c) : tile_count(c));
+    return pairs(c) ? split_blocks(rest_count(c), item_count(c)) : tile_blocks(tile_count(c));
 }
 int step_partials(const lbm_ctx *c) {
     return fluid_partials(c) + node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(c->n_wnodes);
@@ -238,7 +256,9 @@ int step_partials(const lbm_ctx *c) {
 int partial_capacity(const lbm_ctx *c, int64_t n_wnodes) {
     const int nodes = node_blocks((int64_t)c->idx.bnodes.size()) + node_blocks(n_wnodes);
     const int tiles = tile_blocks(std::max<int64_t>((int64_t)c->idx.tiles.size() / TILE_INTS, c->n_tiles_wall));
-    return std::max({c->fluid_blocks + nodes, tiles + nodes, node_blocks(c->idx.n_active)});
+    const int split = std::max(split_blocks((int64_t)c->idx.rest_chunks.size(), (int64_t)c->idx.pair_items.size()),
+                               split_blocks(c->n_rest_wall, c->n_items_wall));
+    return std::max({c->fluid_blocks + nodes, tiles + nodes, split + nodes, node_blocks(c->idx.n_active)});
 }
 
 // Ghost slots and periodic copies of the current buffer from its active cells.
@@ -312,9 +332,11 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     if (tiled(c)) {
         a.tiles = c->d_tiles_wall ? c->d_tiles_wall : c->d_tiles;
         a.ntiles = (int32_t)tile_count(c);
-        if (pairs(c)) {
+        if (pairs(c)) {  // the chunk kernel takes the rest chunks
             a.items = c->d_tiles_wall ? c->d_items_wall : c->d_items;
             a.nitems = (int32_t)item_count(c);
+            a.chunks = c->d_tiles_wall ? c->d_rest_wall : c->d_rest;
+            a.nchunks = (int32_t)rest_count(c);
         }
     }
     const int key = (c->ghost1 ? 2 : 0) + (wide ? 1 : 0);
@@ -409,12 +431,33 @@ lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out) {
     // without allocating tens of gigabytes.
     const char *wide = std::getenv("LBM_WIDE_OFFSETS");
     c->wide_offsets = wide && wide[0] == '1';
-    // LBM_FLUID_KERNEL=chunk runs the chunk fluid kernel where the tile one
-    // would run (for testing both on the same lattices)
+    // LBM_FLUID_KERNEL selects another fluid kernel than the default (FP32:
+    // tile kernel, FP16S / FP64: chunk kernel), for testing every variant on
+    // the same lattices: "chunk", "tile" or "pairs" (FP16S pair + chunk kernel)
     const char *fk = std::getenv("LBM_FLUID_KERNEL");
-    c->chunk_kernel = fk && std::strcmp(fk, "chunk") == 0;
-    c->pair_kernel = !(fk && std::strcmp(fk, "tile") == 0);
+    if (fk && std::strcmp(fk, "chunk") == 0) c->fluid_kernel = FluidKernel::CHUNK;
+    if (fk && std::strcmp(fk, "tile") == 0) c->fluid_kernel = FluidKernel::TILE;
+    if (fk && std::strcmp(fk, "pairs") == 0) c->fluid_kernel = FluidKernel::PAIRS;
     lbm_params_default(&c->params);
+    {
+        // a second stream (at the highest priority) and two events, so that
+        // each step can run its wall-cell and inlet/outlet kernels beside the
+        // fluid kernel; without them (or with LBM_SIDE_STREAM=0 at creation,
+        // for tests) the step runs its kernels in sequence on one stream
+        DeviceGuard g(c->desc.device);
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) hi = 0;
+        const char *ss = std::getenv("LBM_SIDE_STREAM");
+        const bool ok = !(ss && ss[0] == '0') && cudaStreamCreateWithPriority(&c->side.stream, cudaStreamNonBlocking, hi) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            if (c->side.stream) cudaStreamDestroy(c->side.stream);
+            if (c->side.fork) cudaEventDestroy(c->side.fork);
+            c->side = SideStream{};
+        }
+    }
     *out = c;
     return LBM_OK;
 }
@@ -424,6 +467,12 @@ lbm_status lbm_destroy(lbm_ctx *c) {
     DeviceGuard g(c->desc.device);
     cudaStreamSynchronize(c->stream);
     release_geometry(c);
+    if (c->side.stream) {
+        cudaStreamSynchronize(c->side.stream);
+        cudaStreamDestroy(c->side.stream);
+    }
+    if (c->side.fork) cudaEventDestroy(c->side.fork);
+    if (c->side.join) cudaEventDestroy(c->side.join);
     delete c;
     return LBM_OK;
 }
@@ -492,6 +541,7 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
         wn.empty() ? std::vector<int32_t>()
                    : build_tiles(chunks, c->idx.row_nb, c->idx.mask, c->idx.n_row, periodic_rows(c) != 0);
     const std::vector<int2> items = build_pair_items(tiles);
+    const std::vector<int2> rest = build_rest_chunks(chunks, tiles, items);
     c->d_wall_qidx = (int32_t *)dev_alloc(c, qidx.size() * 4);
     c->d_wall_q = (uint8_t *)dev_alloc(c, rec.size());
     c->n_wall_q = n;
@@ -503,6 +553,8 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
         c->d_tiles_wall = (int32_t *)dev_alloc(c, tiles.size() * 4);
         c->n_items_wall = (int64_t)items.size();
         c->d_items_wall = (int2 *)dev_alloc(c, items.size() * 8);
+        c->n_rest_wall = (int64_t)rest.size();
+        c->d_rest_wall = (int2 *)dev_alloc(c, rest.size() * 8);
     }
     const int capacity = partial_capacity(c, c->n_wnodes);
     double *partials = c->d_partials;
@@ -515,7 +567,9 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
         }
     }
     if (!c->d_wall_qidx || !c->d_wall_q ||
-        (!wn.empty() && (!c->d_wnodes || !c->d_chunks_wall || !c->d_tiles_wall || !c->d_items_wall)) || !partials) {
+        (!wn.empty() && (!c->d_wnodes || !c->d_chunks_wall || !c->d_tiles_wall || !c->d_items_wall ||
+                         !c->d_rest_wall)) ||
+        !partials) {
         release_wall_q(c);
         return fail(c, LBM_ERR_OOM, "wall-distance allocation failed");
     }
@@ -534,6 +588,9 @@ lbm_status lbm_set_wall_q(lbm_ctx *c, const int64_t *cells, const uint8_t *q, in
     if (!items.empty())
         CK(cudaMemcpyAsync(c->d_items_wall, items.data(), items.size() * 8, cudaMemcpyHostToDevice, c->stream),
            "copy pair items");
+    if (!rest.empty())
+        CK(cudaMemcpyAsync(c->d_rest_wall, rest.data(), rest.size() * 8, cudaMemcpyHostToDevice, c->stream),
+           "copy rest chunks");
     CK(cudaStreamSynchronize(c->stream), "sync wall distances");
     return LBM_OK;
 }
@@ -560,7 +617,7 @@ int64_t ctx_footprint(const lbm_desc &d, const HostIndex &ix) {
                                              node_blocks(ix.n_active));
     return 2 * pop + (ix.nslots + 2 * MASK_MARGIN) * 4 + (int64_t)ix.row_nb.size() * 4 + (int64_t)ix.chunks.size() * 8 +
            (int64_t)ix.bnodes.size() * 16 + ix.n_active * 4 + (int64_t)ix.tiles.size() * 4 +
-           (int64_t)ix.pair_items.size() * 8 +
+           (int64_t)ix.pair_items.size() * 8 + (int64_t)ix.rest_chunks.size() * 8 +
            blocks * REDUCE_SLOTS * 8 + 64 + 256;
 }
 
@@ -584,11 +641,12 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
     c->d_slot_of_active = (int32_t *)dev_alloc(c, c->idx.slot_of_active.size() * 4);
     c->d_tiles = (int32_t *)dev_alloc(c, c->idx.tiles.size() * 4);
     c->d_items = (int2 *)dev_alloc(c, c->idx.pair_items.size() * 8);
+    c->d_rest = (int2 *)dev_alloc(c, c->idx.rest_chunks.size() * 8);
     c->d_partials = (double *)dev_alloc(c, (size_t)c->nblocks * REDUCE_SLOTS * 8);
     c->d_health = (double *)dev_alloc(c, 8 * 8);
     c->d_status = (uint32_t *)dev_alloc(c, 256);
     if (!c->f[0] || !c->f[1] || !c->d_mask || !c->d_row_nb || !c->d_chunks || !c->d_bnodes || !c->d_slot_of_active ||
-        !c->d_tiles || !c->d_items || !c->d_partials || !c->d_health || !c->d_status) {
+        !c->d_tiles || !c->d_items || !c->d_rest || !c->d_partials || !c->d_health || !c->d_status) {
         release_geometry(c);
         return fail(c, LBM_ERR_OOM, "device allocation failed in lbm_set_geometry");
     }
@@ -615,6 +673,10 @@ lbm_status ctx_install_index(lbm_ctx *c, HostIndex &&idx) {
         CK(cudaMemcpyAsync(c->d_items, c->idx.pair_items.data(), c->idx.pair_items.size() * 8,
                            cudaMemcpyHostToDevice, c->stream),
            "copy pair items");
+    if (!c->idx.rest_chunks.empty())
+        CK(cudaMemcpyAsync(c->d_rest, c->idx.rest_chunks.data(), c->idx.rest_chunks.size() * 8,
+                           cudaMemcpyHostToDevice, c->stream),
+           "copy rest chunks");
     // Padding slots are never read by the step kernel; zero both buffers so
     // that checkpoints and dumps are deterministic.
     CK(cudaMemsetAsync(c->f_raw[0], 0, raw_pop_bytes(c), c->stream), "clear f0");
@@ -856,8 +918,13 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
             a.flags |= STEP_STATS | (c->stats_ncomp == STATS_FULL ? STEP_STATS_FULL : 0);
             ++c->stats_samples;
         }
-        CK(DISPATCH(c->desc.precision, launch_step, a, c->ghost1, c->stream), "step kernel");
-        if (check) CK(launch_finalize(c->d_partials, step_partials(c), c->d_health, c->d_status, c->stream), "finalize");
+        int launched = 0;
+        CK(DISPATCH(c->desc.precision, launch_step, a, c->ghost1, c->stream, &launched, &c->side), "step kernel");
+        c->kernel_launches += launched;
+        if (check) {
+            CK(launch_finalize(c->d_partials, step_partials(c), c->d_health, c->d_status, c->stream), "finalize");
+            ++c->kernel_launches;
+        }
         c->cur = 1 - c->cur;
         c->t = t_new;
     }
@@ -1161,6 +1228,12 @@ lbm_status lbm_layout_info(lbm_ctx *c, int64_t *slots, int64_t *buffer_bytes, in
     if (slots) *slots = c->idx.nslots;
     if (buffer_bytes) *buffer_bytes = (int64_t)pop_bytes(c);
     if (device_bytes) *device_bytes = c->device_bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_kernel_launches(lbm_ctx *c, int64_t *n) {
+    if (!c || !n) return LBM_ERR_ARG;
+    *n = c->kernel_launches;
     return LBM_OK;
 }
 

@@ -270,6 +270,7 @@ std::string build_index(const uint8_t *flags, int nx, int ny, int nz, int period
     if ((int64_t)out.chunks.size() > (int64_t)INT32_MAX / CHUNK) return "too many chunks";
     out.tiles = build_tiles(out.chunks, out.row_nb, out.mask, F.np, F.pp);
     out.pair_items = build_pair_items(out.tiles);
+    out.rest_chunks = build_rest_chunks(out.chunks, out.tiles, out.pair_items);
     return "";
 }
 
@@ -277,16 +278,30 @@ std::vector<int2> build_pair_items(const std::vector<int32_t> &tiles) {
     const int64_t nt = (int64_t)tiles.size() / TILE_INTS;
     auto fast = [&](int64_t t) { return ((uint32_t)tiles[(size_t)t * TILE_INTS] & TILE_FAST) != 0u; };
     std::vector<int2> items;
-    for (int64_t t = 0; t < nt;) {
-        if (fast(t) && t + 1 < nt && fast(t + 1)) {
+    for (int64_t t = 0; t + 1 < nt;) {
+        if (fast(t) && fast(t + 1)) {
             items.push_back(make_int2((int)t, (int)t + 1));
             t += 2;
         } else {
-            items.push_back(make_int2((int)t, -1));
             t += 1;
         }
     }
     return items;
+}
+
+std::vector<int2> build_rest_chunks(const std::vector<int2> &chunks, const std::vector<int32_t> &tiles,
+                                    const std::vector<int2> &pairs) {
+    const int64_t nt = (int64_t)tiles.size() / TILE_INTS;
+    std::vector<uint8_t> paired((size_t)nt, 0);
+    for (const int2 &it : pairs) paired[(size_t)it.x] = paired[(size_t)it.y] = 1;
+    std::vector<int2> rest;
+    size_t c = 0;  // first chunk of tile t: the tiles hold the chunks in order, 8 present lanes each
+    for (int64_t t = 0; t < nt; ++t) {
+        const size_t n = (size_t)__builtin_popcount((uint32_t)tiles[(size_t)t * TILE_INTS + 2]) / CHUNK;
+        if (!paired[(size_t)t]) rest.insert(rest.end(), chunks.begin() + c, chunks.begin() + c + n);
+        c += n;
+    }
+    return rest;
 }
 
 std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
@@ -493,19 +508,34 @@ std::string validate_index(const HostIndex &ix, const uint8_t *flags, int nx, in
     }
     for (int64_t b = 0; b < (int64_t)in_tile.size(); ++b)
         if ((flags[b] == LBM_FLUID) != (in_tile[b] == 1)) return "fluid cell not in exactly one tile lane";
-    // pair-kernel items: every tile exactly once; both tiles of a pair fast
-    std::vector<uint8_t> in_item((size_t)nt, 0);
+    // FP16S split: pairs of fast tiles, each tile in at most one pair; the
+    // chunks of the pairs' tiles (four full chunks from p0, on the tile's own
+    // row) and the rest chunks together are the chunk list, as a multiset
+    std::vector<uint8_t> in_pair((size_t)nt, 0);
+    using ChunkKey = std::pair<int64_t, uint32_t>;  // (row base slot, chunk word)
+    std::vector<ChunkKey> split, whole;
     for (const int2 &it : ix.pair_items) {
-        if (it.x < 0 || it.x >= nt || in_item[(size_t)it.x]++) return "pair item tile";
-        if (it.y >= 0) {
-            if (it.y >= nt || in_item[(size_t)it.y]++) return "pair item tile";
-            if (!((uint32_t)ix.tiles[(size_t)it.x * TILE_INTS] & TILE_FAST) ||
-                !((uint32_t)ix.tiles[(size_t)it.y * TILE_INTS] & TILE_FAST))
-                return "pair item of a tile that is not fast";
+        if (it.x < 0 || it.x >= nt || it.y < 0 || it.y >= nt || it.x == it.y) return "pair item tile";
+        if (in_pair[(size_t)it.x]++ || in_pair[(size_t)it.y]++) return "tile in two pair items";
+        for (const int t : {it.x, it.y}) {
+            const int32_t *rec = &ix.tiles[(size_t)t * TILE_INTS];
+            if (!((uint32_t)rec[0] & TILE_FAST)) return "pair item of a tile that is not fast";
+            const uint32_t p0 = (uint32_t)rec[0] & ~TILE_FAST;
+            for (uint32_t k = 0; k < 4; ++k)
+                split.emplace_back(rec[3 + 4], (p0 + CHUNK * k) | (0xFFu << CHUNK_LANES_SHIFT));
         }
     }
-    for (int64_t t = 0; t < nt; ++t)
-        if (in_item[(size_t)t] != 1) return "tile not in exactly one pair item";
+    auto key = [&](const int2 &c) -> ChunkKey {
+        return {ix.row_nb[(size_t)c.x * ROW_RECORD_INTS + 4], (uint32_t)c.y};
+    };
+    for (const int2 &c : ix.rest_chunks) {
+        if (c.x < 0 || (int64_t)c.x >= nrows) return "rest chunk row";
+        split.push_back(key(c));
+    }
+    for (const int2 &c : ix.chunks) whole.push_back(key(c));
+    std::sort(split.begin(), split.end());
+    std::sort(whole.begin(), whole.end());
+    if (split != whole) return "pair tiles and rest chunks do not cover the chunks exactly once";
 
     return "";
 }

@@ -1409,24 +1409,19 @@ __device__ __forceinline__ void pair_update(const StepArgs &a, int t, int k, dou
     for (int q = 0; q < 6; ++q) hv[q] = q == 4 ? fmax(h0[q], h1[q]) : h0[q] + h1[q];
 }
 
-// FP16S fluid kernel over work items, one per warp: an item of two fast
-// tiles runs on the pair path (16 threads per tile, two cells per thread); an
-// item of one tile (a tile with walls, or a fast tile without a fast
-// neighbour in the row order) runs on the one-cell tile path.  Items follow
-// the tiles' row order, and the branch is uniform over the warp.
+// FP16S pair kernel: one pair of fast tiles per warp (in row order), 16
+// threads per tile, two cells per thread.  Every other cell of the lattice
+// is updated by the chunk kernel over the remaining chunks, in a launch of
+// its own: one instruction stream per kernel, each at its own register
+// budget.
 template <int AX>
 __global__ void __launch_bounds__(STEP_THREADS, LBM_PAIR_MIN_BLOCKS) k_step_pairs(const StepArgs a) {
-    using O = TileOut<2>;
-    __shared__ __align__(16) typename O::T staged_out[STEP_THREADS / 32][O::ELEMS];
     const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
     const int w = (int)blockIdx.x * (STEP_THREADS / 32) + warp;
     double hv[6] = {0, 0, 0, 0, 0, 0};
     if (w < a.nitems) {
         const int2 item = __ldg(a.items + w);
-        if (item.y >= 0)
-            pair_update<AX>(a, lane < 16 ? item.x : item.y, lane & 15, hv);
-        else
-            tile_update<2, AX>(a, item.x, lane, staged_out[warp], hv);
+        pair_update<AX>(a, lane < 16 ? item.x : item.y, lane & 15, hv);
     }
     if (a.flags & STEP_REDUCE) block_reduce_write(hv, a.partials);
 }
@@ -1633,49 +1628,96 @@ int step_prefetch_ahead(bool ghost1, bool wide, int device) {
     return (int)((int64_t)per_sm * sms * pct / 100);
 }
 
+// The wall-cell and inlet/outlet kernels of a step (those not fused into
+// the fluid kernel), on stream sn.
 template <int P, bool G, bool WD, int AX>
-void launch_step_ax(const StepArgs &a, cudaStream_t s) {
+void launch_node_kernels(const StepArgs &a, cudaStream_t sn, bool boundary, int &launches) {
+    if (a.nwnodes > 0) {  // cells with interpolated walls
+        k_wall<P, G, WD, AX><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, sn>>>(a);
+        ++launches;
+    }
+    if (boundary && a.nbnodes > 0) {
+        k_boundary<P, G, WD, AX><<<(a.nbnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, sn>>>(a);
+        ++launches;
+    }
+}
+
+// One step: the node kernels go first, on the side stream when there is one
+// (forked from s and joined back into it at the end), so that their few
+// long-latency blocks run beside the fluid kernel instead of after it.  All
+// kernels of a step read the input buffer only and write disjoint output
+// elements and partial sums, so their order does not change any result.
+template <int P, bool G, bool WD, int AX>
+cudaError_t launch_step_ax(const StepArgs &a, cudaStream_t s, const SideStream *side, int &launches) {
     const int bb = (int)((a.nbnodes + STEP_THREADS - 1) / STEP_THREADS);
+    const bool tiled = G && !WD && P != 0 && a.tiles != nullptr;
+    const bool fused = !tiled && LBM_FUSE_BOUNDARY && P == 1 && a.nchunks > 0;  // nodes in trailing blocks of k_step
+    const bool nodes = a.nwnodes > 0 || (bb > 0 && !fused);
+    const bool aside = nodes && side && side->stream;
+    cudaStream_t sn = s;
+    if (aside) {
+        cudaError_t e = cudaEventRecord(side->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side->stream, side->fork, 0);
+        if (e != cudaSuccess) return e;
+        sn = side->stream;
+    }
+    launch_node_kernels<P, G, WD, AX>(a, sn, !fused, launches);
     if constexpr (G && !WD && P != 0) {
-        if (a.tiles) {  // the tile fluid kernel; inlet/outlet nodes and wall cells in launches of their own
+        if (tiled) {
             if constexpr (P == 2) {
-                if (a.items) {  // FP16S: pairs of fast tiles two cells per thread
-                    if (a.nitems > 0) k_step_pairs<AX><<<tile_blocks(a.nitems), STEP_THREADS, 0, s>>>(a);
+                if (a.items) {  // FP16S split: pairs of fast tiles, two cells per thread; the other chunks
+                    if (a.nchunks > 0) {
+                        k_step<P, G, WD, AX><<<step_blocks(a.nchunks), STEP_THREADS, 0, s>>>(a);
+                        ++launches;
+                    }
+                    if (a.nitems > 0) {
+                        StepArgs b = a;  // partial sums after the chunk kernel's
+                        b.partials = a.partials + (size_t)step_blocks(a.nchunks) * REDUCE_SLOTS;
+                        k_step_pairs<AX><<<tile_blocks(a.nitems), STEP_THREADS, 0, s>>>(b);
+                        ++launches;
+                    }
                 } else if (a.ntiles > 0) {
                     k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
+                    ++launches;
                 }
             } else if (a.ntiles > 0) {
                 k_step_tiles<P, AX><<<tile_blocks(a.ntiles), STEP_THREADS, 0, s>>>(a);
+                ++launches;
             }
-            if (a.nwnodes > 0)
-                k_wall<P, G, WD, AX><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
-            if (bb > 0) k_boundary<P, G, WD, AX><<<bb, STEP_THREADS, 0, s>>>(a);
-            return;
         }
     }
-    const bool fused = LBM_FUSE_BOUNDARY && P == 1 && a.nchunks > 0;  // nodes in trailing blocks of k_step
-    if (a.nchunks > 0) k_step<P, G, WD, AX><<<step_blocks(a.nchunks) + (fused ? bb : 0), STEP_THREADS, 0, s>>>(a);
-    if (a.nwnodes > 0)  // cells with interpolated walls
-        k_wall<P, G, WD, AX><<<(a.nwnodes + STEP_THREADS - 1) / STEP_THREADS, STEP_THREADS, 0, s>>>(a);
-    if (bb > 0 && !fused) k_boundary<P, G, WD, AX><<<bb, STEP_THREADS, 0, s>>>(a);
+    if (!tiled && a.nchunks > 0) {
+        k_step<P, G, WD, AX><<<step_blocks(a.nchunks) + (fused ? bb : 0), STEP_THREADS, 0, s>>>(a);
+        ++launches;
+    }
+    if (aside) {
+        cudaError_t e = cudaEventRecord(side->join, sn);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side->join, 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int P, bool G, bool WD>
-void launch_step_rows(const StepArgs &a, cudaStream_t s) {
-    if (a.row_axis == 2)
-        launch_step_ax<P, G, WD, 2>(a, s);
-    else
-        launch_step_ax<P, G, WD, 0>(a, s);
+cudaError_t launch_step_rows(const StepArgs &a, cudaStream_t s, const SideStream *side, int &launches) {
+    return a.row_axis == 2 ? launch_step_ax<P, G, WD, 2>(a, s, side, launches)
+                           : launch_step_ax<P, G, WD, 0>(a, s, side, launches);
 }
 
+// One time step of a lattice; launches (if not NULL) is increased by the
+// number of kernels launched; side (if not NULL) is the stream of the
+// wall-cell and inlet/outlet kernels.
 template <int P>
-cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s) {
+cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s, int *launches, const SideStream *side) {
     const bool wide = a.wide_offsets || a.stride > MAX_SLOTS_32;
+    int n = 0;
+    cudaError_t e;
     if (ghost1)
-        wide ? launch_step_rows<P, true, true>(a, s) : launch_step_rows<P, true, false>(a, s);
+        e = wide ? launch_step_rows<P, true, true>(a, s, side, n) : launch_step_rows<P, true, false>(a, s, side, n);
     else
-        wide ? launch_step_rows<P, false, true>(a, s) : launch_step_rows<P, false, false>(a, s);
-    return cudaGetLastError();
+        e = wide ? launch_step_rows<P, false, true>(a, s, side, n) : launch_step_rows<P, false, false>(a, s, side, n);
+    if (launches) *launches += n;
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int P>
@@ -1746,7 +1788,7 @@ cudaError_t launch_init_eq(void *f, const int32_t *soa, int64_t n, int64_t strid
 }
 
 #define LBM_INSTANTIATE(P)                                                                                         \
-    template cudaError_t launch_step<P>(const StepArgs &, bool, cudaStream_t);                                     \
+    template cudaError_t launch_step<P>(const StepArgs &, bool, cudaStream_t, int *, const SideStream *);                                     \
     template int step_fluid_blocks<P>(int32_t);                                                                     \
     template int step_prefetch_ahead<P>(bool, bool, int);                                                          \
     template cudaError_t launch_reduce<P>(const void *, const int32_t *, int64_t, int64_t, float, double *,       \

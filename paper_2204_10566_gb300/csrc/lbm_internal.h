@@ -98,8 +98,24 @@ constexpr uint32_t TILE_FAST = 1u << 31;
 std::vector<int32_t> build_tiles(const std::vector<int2> &chunks, const std::vector<int32_t> &row_nb,
                                  const std::vector<uint32_t> &mask, int n_row, bool periodic_row);
 // Work items of the FP16S pair kernel over tile records in row order: (t, t + 1)
-// for two consecutive fast tiles, (t, -1) for any other tile.
+// for two consecutive fast tiles, taken greedily from the start.
 std::vector<int2> build_pair_items(const std::vector<int32_t> &tiles);
+// The chunks of every tile that is in no pair item, in order: the chunk
+// kernel's list beside the pair kernel.
+std::vector<int2> build_rest_chunks(const std::vector<int2> &chunks, const std::vector<int32_t> &tiles,
+                                    const std::vector<int2> &pairs);
+
+// Fluid kernel of the FP32 / FP16S steps: AUTO is the tile kernel in FP32
+// and the chunk kernel in FP16S; the others are kept for testing.
+enum class FluidKernel { AUTO, CHUNK, TILE, PAIRS };
+
+// A second stream and its fork / join events: a step's wall-cell and
+// inlet/outlet kernels run on it beside the fluid kernel.  They read the
+// same input buffer and write other slots and other partial sums.
+struct SideStream {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
 
 // Flow parameters in the arithmetic precision of a kernel.
 template <class R>
@@ -144,7 +160,7 @@ struct alignas(16) StepArgs {
     int32_t wide_offsets;      // 1: 64-bit element offsets even when 32 bits would do (LBM_WIDE_OFFSETS=1)
     const int32_t *tiles;      // tile records of the tile fluid kernels (NULL: chunk kernel)
     int32_t ntiles;
-    const int2 *items;         // FP16S work items of the pair kernel (NULL: tile kernel)
+    const int2 *items;         // FP16S pairs of fast tiles (NULL: tile kernel); chunks then holds the rest
     int32_t nitems;
 };
 
@@ -154,7 +170,8 @@ struct alignas(16) StepArgs {
 constexpr int64_t MAX_SLOTS_32 = (int64_t)0xFFFFFFFFu / 27 - 64;
 
 template <int P>
-cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s);
+cudaError_t launch_step(const StepArgs &a, bool ghost1, cudaStream_t s, int *launches = nullptr,
+                        const SideStream *side = nullptr);
 // L2 prefetch lookahead of the fluid kernel in blocks: a fixed share of the
 // blocks resident on the device at once (occupancy x SM count); 0 = off.
 template <int P>
@@ -209,7 +226,8 @@ struct HostIndex {
     std::vector<int32_t> row_nb;          // [rows][ROW_RECORD_INTS]
     std::vector<int2> chunks;             // chunk records (fluid cells)
     std::vector<int32_t> tiles;           // [tiles][TILE_INTS] records of the tile fluid kernels
-    std::vector<int2> pair_items;         // work items of the FP16S pair kernel
+    std::vector<int2> pair_items;         // pairs of fast tiles, for the FP16S pair kernel
+    std::vector<int2> rest_chunks;        // chunks of the other tiles, for the chunk kernel beside it
     std::vector<int4> bnodes;             // inlet/outlet nodes: x, row, slot, link word
     std::vector<uint32_t> mask;           // [nslots]
     std::vector<int32_t> slot_of_active;  // [n_active], active order = increasing box index

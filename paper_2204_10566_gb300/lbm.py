@@ -135,6 +135,7 @@ _SIGS = {
     "lbm_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lbm_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lbm_layout_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lbm_kernel_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "lbm_totals_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.c_int64, C.c_int64, C.c_void_p,
                                      C.c_void_p]),
     "lbm_server_create": (C.c_int, [C.POINTER(lbm_server_desc), C.POINTER(C.c_void_p)]),
@@ -501,6 +502,12 @@ class Lattice:
         s, b, d = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(self.lib.lbm_layout_info(self.ctx, C.byref(s), C.byref(b), C.byref(d)))
         return dict(slots=s.value, buffer_bytes=b.value, device_bytes=d.value)
+
+    def kernel_launches(self):
+        """Kernels lbm_step has launched on this lattice so far."""
+        n = C.c_int64()
+        self._check(self.lib.lbm_kernel_launches(self.ctx, C.byref(n)))
+        return n.value
 
 
 def make_request(flags, steps, precision="fp32", periodic=0, fp16_scale=0.0, **params):

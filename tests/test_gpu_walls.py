@@ -162,3 +162,28 @@ def test_wall_cells_enter_health_and_statistics(lbm):
     assert np.abs(h[1:4] - (rho[:, None] * u).sum(axis=0)).max() < 1e-12 * rho.sum()
     m1, _, n = G.stats_get()
     assert n == 6 and np.abs(m1 - acc / 6).max() < 1e-15
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16s"])
+def test_side_stream_changes_no_bit(lbm, precision, monkeypatch):
+    """The wall-cell and inlet/outlet kernels run on a second stream beside
+    the fluid kernel; with them in sequence on one stream (LBM_SIDE_STREAM=0)
+    the populations, the health record and the statistics are bitwise the
+    same."""
+    D, d, L = 12, 4, 40
+    flags = I.nozzle_flags(D, d, L)
+    cells, q = I.nozzle_wall_q(D, d, L)
+    out = []
+    for side in ("1", "0"):
+        monkeypatch.setenv("LBM_SIDE_STREAM", side)
+        G = gpu_lattice(lbm, flags, precision, 0.02, profile="parabolic", u_in=0.02, d_in=float(D),
+                        noise_amp=0.02, seed=3)
+        G.set_wall_q(cells, q)
+        G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
+        G.set_check_every(3)
+        G.stats_begin(1)
+        G.step(40).sync()
+        out.append((G.get_populations(BOX), G.health(), G.stats_get(BOX)[0]))
+        G.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)

@@ -47,6 +47,9 @@ MUTANTS = {
         "for (int p0 = (int)std::floor(act_lo[r] / (double)CHUNK) * CHUNK; p0 <= act_hi[r]; p0 += CHUNK) {",
         "for (int p0 = act_lo[r]; p0 <= act_hi[r]; p0 += CHUNK) {"),
     "z_rows_cross_directions_swapped": ("            cp = cz, ca = cx, cb = cy;", "            cp = cz, ca = cy, cb = cx;"),
+    "pair_items_overlap": ("            t += 2;\n", "            t += 1;\n"),
+    "rest_chunks_counted_from_fluid_lanes": ("(uint32_t)tiles[(size_t)t * TILE_INTS + 2]) / CHUNK",
+                                             "(uint32_t)tiles[(size_t)t * TILE_INTS + 1]) / CHUNK"),
     "z_rows_storage_order": ("        return ax == 0 ? box_index(p, a, b, nx, ny) : box_index(a, b, p, nx, ny);",
                              "        return ax == 0 ? box_index(p, a, b, nx, ny) : box_index(b, a, p, nx, ny);"),
 }
