@@ -356,6 +356,23 @@ void ctx_step_args(lbm_ctx *c, StepArgs *out) {
     *out = a;
 }
 
+// The same arguments for the chunk kernel's view of the lattice (every chunk,
+// every inlet/outlet node, no tiles, no pair items): the request server's
+// multi-lattice kernels walk the lattice that way whatever fluid kernel the
+// context's own steps run.
+void ctx_chunk_step_args(lbm_ctx *c, StepArgs *out) {
+    ctx_step_args(c, out);
+    out->chunks = c->d_chunks_wall ? c->d_chunks_wall : c->d_chunks;
+    out->nchunks = (int32_t)c->idx.chunks.size();
+    out->bnodes = c->d_bnodes;
+    out->nbnodes = (int32_t)c->idx.bnodes.size();
+    out->tiles = nullptr;
+    out->ntiles = 0;
+    out->items = nullptr;
+    out->nitems = 0;
+    out->fluid_blocks = c->fluid_blocks;
+}
+
 void ctx_advance(lbm_ctx *c, int64_t steps) {
     c->t += steps;
     if (steps & 1) c->cur = 1 - c->cur;

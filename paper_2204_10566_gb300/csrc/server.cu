@@ -34,6 +34,10 @@ namespace lbm {
 // other value must be a positive power of two; returns 0 when invalid.
 float resolve_fp16_scale(float s);
 
+// A context's step arguments in the chunk kernel's view (api.cu): every
+// chunk and every inlet/outlet node, whichever fluid kernel its own steps run.
+void ctx_chunk_step_args(lbm_ctx *c, StepArgs *out);
+
 constexpr int MAX_SLOTS = LBM_SERVER_MAX_SLOTS;
 constexpr int NGROUPS = 2;  // 0: FP32, 1: FP16S
 
@@ -554,7 +558,7 @@ lbm_status lbm_server_tick(lbm_server *s, int32_t *running, int32_t *queued) {
         GroupTable *tab = s->h_tab[r->group];
         flag_of[k] = r->group * MAX_SLOTS + tab->n_domains;
         DomainEntry &e = tab->d[tab->n_domains++];
-        ctx_step_args(r->ctx, &e.a);
+        ctx_chunk_step_args(r->ctx, &e.a);
         e.a.status = s->d_flags + flag_of[k];  // the lattice's health flag
         e.t_base = r->steps_done;
         e.steps = (int32_t)std::min<int64_t>(K, r->req.steps - r->steps_done);

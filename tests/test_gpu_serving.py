@@ -38,6 +38,23 @@ MIX = [spec(0, "nozzle", 8, 800.0, 101, "fp32"), spec(1, "pipe", 6, 2000.0, 60, 
        spec(4, "nozzle", 6, 6500.0, 75, "fp16s")]
 
 
+@pytest.mark.parametrize("kernel", ["tile", "pairs"])
+def test_server_independent_of_the_contexts_fluid_kernel(mods, monkeypatch, kernel):
+    """The server steps every lattice with its own multi-lattice kernels over
+    all chunks and all inlet/outlet nodes, whatever fluid kernel the
+    contexts would run alone (LBM_FLUID_KERNEL, read at context creation,
+    changes a context's own chunk and node lists): the results are bitwise
+    those of the default."""
+    lbm, serving = mods
+    ref = serving.run_stream([dict(s) for s in MIX], budget_bytes=4 << 30, steps_per_tick=16)
+    monkeypatch.setenv("LBM_FLUID_KERNEL", kernel)
+    got = serving.run_stream([dict(s) for s in MIX], budget_bytes=4 << 30, steps_per_tick=16)
+    for k in range(len(MIX)):
+        (ra, ua), (rb, ub) = ref["results"][k]["result"], got["results"][k]["result"]
+        assert np.array_equal(ra, rb) and np.array_equal(ua, ub)
+        assert np.abs(ua).max() > 0
+
+
 def test_result_alone_equals_result_in_the_mix(mods):
     """Each lattice is updated by the same device code whatever else is
     resident: the result of a request served alone equals, bit for bit, its
