@@ -5,7 +5,7 @@
  * (arXiv 2204.10566).
  *
  * One call of lbm_step advances every active cell of the lattice by one time
- * step with a single fused pull-stream/collide kernel:
+ * step of the pull-stream/collide update:
  *   f_i(x + c_i, t + 1) - f_i(x, t) = T^-1 S T (f^eq(rho, u) - f)(x, t)
  * (Sec. 2.1, MRT evolution eq.), T the central Hermite transform
  * (Sec. 2.1, central moment eq.; Appendix A), f^eq the full Hermite expansion
@@ -32,7 +32,11 @@
  *     error, lbm_last_error(ctx) describes it; the string is owned by ctx and
  *     valid until the next call on ctx.
  *   - Device work is enqueued on the context's stream.  Calls that return
- *     host data synchronise that stream; lbm_step does not.
+ *     host data synchronise that stream; lbm_step does not.  lbm_step also
+ *     uses a second stream that the context owns: each step forks onto it
+ *     with an event recorded on the context's stream and joins back with
+ *     another before the step ends, so the step stays ordered on the
+ *     context's stream and can be captured into a CUDA graph there.
  *   - A context is not thread-safe: one host thread at a time.
  */
 #ifndef LBM_H
@@ -126,10 +130,15 @@ const char *lbm_status_string(lbm_status s);
 void lbm_params_default(lbm_params *p);
 
 /* Create a context on desc->device bound to desc->stream.  Allocates nothing
- * on the device until lbm_set_geometry.  *out receives the context.
+ * on the device until lbm_set_geometry, apart from the second stream (highest
+ * priority) and its two events; if those cannot be created, or with
+ * LBM_SIDE_STREAM=0 in the environment at creation, every kernel of a step
+ * runs on desc->stream in sequence.  *out receives the context.
  * Lattices of 2^32 / 27 slots or more step with 64-bit element offsets; with
  * the environment variable LBM_WIDE_OFFSETS=1 at creation, every lattice
- * does (for testing that path on small lattices).
+ * does (for testing that path on small lattices).  LBM_FLUID_KERNEL at
+ * creation selects another fluid kernel than the default for tests and
+ * measurements: "chunk", "tile" or "pairs" (same results within rounding).
  * Errors: LBM_ERR_ARG (bad sizes, precision, scale), LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_desc *desc, lbm_ctx **out);
 
@@ -252,8 +261,12 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int32_t layout);
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int32_t layout);
 
 /* Enqueue n >= 0 time steps on the context stream (asynchronous).  Each step
- * is one fused stream-collide kernel (with the boundary nodes folded in); the
- * health check and the statistics sampling ride on the same kernel when due.
+ * is the fluid kernel (FP32: one warp per tile of up to 32 cells of a row;
+ * FP16S, FP64 and general ghost rates: one thread per cell) on the context's
+ * stream, and the inlet/outlet and interpolated-wall kernels on the second
+ * stream beside it; they read the same input and write disjoint outputs, so
+ * their order changes no result.  The health check and the statistics
+ * sampling ride on these kernels when due.
  * Errors: LBM_ERR_STATE (no geometry / params / init), LBM_ERR_CUDA. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
 

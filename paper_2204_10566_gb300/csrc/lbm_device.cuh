@@ -9,9 +9,12 @@
 //   second-order moments relaxed at omega, orders 3..6 at the ghost rates
 //   (default 1, Appendix A).
 //
-// GB300 design: one thread per active cell, pull scheme over a fluid-only
-// slot layout (rows of x-contiguous cells), structure-of-arrays populations
-// stored as deviations from the lattice weights.  Every pull source has a
+// GB300 design: pull scheme over a fluid-only slot layout (rows of cells
+// contiguous along the lattice's longer axis), structure-of-arrays
+// populations stored as deviations from the lattice weights; one warp per
+// tile of up to 32 cells of a row (FP32) or one thread per cell (FP16S,
+// FP64), with the inlet/outlet nodes and the interpolated-wall cells in
+// kernels of their own on a second stream.  Every pull source has a
 // slot (wall links read a ghost slot the cell filled with its reflected
 // population in the previous step), so the gather is 27 unconditional
 // coalesced loads at nb[j] + x - cx.  Because T(u) is the tensor product of
@@ -36,11 +39,12 @@
 #endif
 // The same for the kernel of the cells with interpolated walls, which keeps
 // the wall record and the own-slot values of a cell in registers as well.
-// In FP32 the inlet/outlet nodes ride in trailing blocks of the fluid kernel
-// (one launch per step) instead of a launch of their own: +2 % on the Re 3500
-// nozzle, although the node path spills at the fluid path's register cap.
-// In FP16S the fused kernel spilled in the fluid path too, and FP64's
-// uncapped fluid path would lose occupancy, so both keep the separate launch.
+// When the FP32 chunk kernel runs (LBM_FLUID_KERNEL=chunk), the inlet/outlet
+// nodes ride in its trailing blocks instead of a launch of their own: +2 % on
+// the Re 3500 nozzle, although the node path spills at the fluid path's
+// register cap.  In FP16S the fused kernel spilled in the fluid path too, and
+// FP64's uncapped fluid path would lose occupancy, so both keep the separate
+// launch.
 // FP16S: gather and own-slot stores addressed from one pointer per line
 // (the three values of a line sit at +1, +stride, +2 stride - 1 from it):
 // +4 % / +7 % on the Re 3500 / Re 6500 nozzles, while FP32 lost 4 %, so FP32
@@ -63,8 +67,8 @@
 // L2 prefetch lookahead of the fluid kernel, in percent of the blocks
 // resident on the device (0 disables the prefetch).  At 8 blocks per SM the
 // FP32 kernel keeps enough loads in flight on its own (the prefetch measured
-// neutral, +60 MB of DRAM reads per Re 3500 step), and FP16S is issue-bound
-// and runs 2-3 % slower with it; both default to off.
+// neutral, +60 MB of DRAM reads per Re 3500 step), and FP16S runs 2-3 %
+// slower with it; both default to off.
 #ifndef LBM_PREFETCH_AHEAD_PCT
 #define LBM_PREFETCH_AHEAD_PCT 0
 #endif
