@@ -13,6 +13,11 @@
 
 #include "lbm_internal.h"
 
+namespace lbm {
+// Per-cell (rho, u) in active order -> rho[n], u[n][3] on the device (common.cu).
+cudaError_t launch_split_moments(const double *in, int64_t n, double *rho, double *u, cudaStream_t s);
+}  // namespace lbm
+
 using namespace lbm;
 
 struct lbm_ctx {
@@ -839,14 +844,21 @@ lbm_status lbm_init_fields(lbm_ctx *c, const double *rho, const double *u, int32
         return fail(c, LBM_ERR_ARG, "need rho, u and a valid layout");
     DeviceGuard g(c->desc.device);
     const int64_t n = c->idx.n_active;
-    std::vector<double> h((size_t)n * 4);
-    for_active(c, layout, [&](int64_t k, int64_t r) {
-        h[(size_t)k] = rho[r];
-        for (int a = 0; a < 3; ++a) h[(size_t)n + 3 * (size_t)k + a] = u[3 * r + a];
-    });
     double *d = (double *)dev_alloc(c, (size_t)n * 4 * 8);
     if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
-    cudaError_t e = cudaMemcpyAsync(d, h.data(), (size_t)n * 4 * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e;
+    if (layout == LBM_LAYOUT_ACTIVE) {  // the caller's arrays are already in the device's order: copy them as they are
+        e = cudaMemcpyAsync(d, rho, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, u, (size_t)n * 3 * 8, cudaMemcpyHostToDevice, c->stream);
+    } else {
+        std::vector<double> h((size_t)n * 4);
+        for_active(c, layout, [&](int64_t k, int64_t r) {
+            h[(size_t)k] = rho[r];
+            for (int a = 0; a < 3; ++a) h[(size_t)n + 3 * (size_t)k + a] = u[3 * r + a];
+        });
+        e = cudaMemcpyAsync(d, h.data(), (size_t)n * 4 * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // h leaves scope
+    }
     c->cur = 0;
     if (e == cudaSuccess)
         e = DISPATCH(c->desc.precision, launch_init_eq, c->f[0], c->d_slot_of_active, n, c->idx.nslots,
@@ -988,6 +1000,21 @@ lbm_status lbm_get_moments(lbm_ctx *c, double *rho, double *u, int32_t layout) {
     DeviceGuard g(c->desc.device);
     const int64_t n = c->idx.n_active;
     const size_t bytes = (size_t)n * 4 * 8;
+    if (layout == LBM_LAYOUT_ACTIVE) {
+        // split on the device, then one copy straight into each of the caller's arrays
+        double *d = (double *)dev_alloc(c, 2 * bytes);
+        if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
+        double *dr = d + 4 * n, *du = d + 5 * n;
+        cudaError_t e = DISPATCH(c->desc.precision, launch_moments, c->f[c->cur], c->d_slot_of_active, n,
+                                 c->idx.nslots, 1.0f / fp16_scale(c), d, c->stream);
+        if (e == cudaSuccess) e = launch_split_moments(d, n, dr, du, c->stream);
+        if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, dr, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, (size_t)n * 3 * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, d, 2 * bytes);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get moments");
+        return LBM_OK;
+    }
     double *d = (double *)dev_alloc(c, bytes);
     if (!d) return fail(c, LBM_ERR_OOM, "staging allocation failed");
     std::vector<double> h((size_t)n * 4);

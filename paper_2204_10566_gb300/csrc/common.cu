@@ -64,4 +64,21 @@ cudaError_t launch_stats_mean(const double *stats, int ncomp, const int32_t *slo
     return cudaGetLastError();
 }
 
+// Split per-cell moments (rho, ux, uy, uz) in active order into rho[n] and
+// u[n][3], so that both go to the caller's host arrays in one copy each.
+__global__ void k_split_moments(const double *in, int64_t n, double *rho, double *u) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    rho[k] = in[4 * k];
+    u[3 * k] = in[4 * k + 1];
+    u[3 * k + 1] = in[4 * k + 2];
+    u[3 * k + 2] = in[4 * k + 3];
+}
+
+cudaError_t launch_split_moments(const double *in, int64_t n, double *rho, double *u, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_split_moments<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, rho, u);
+    return cudaGetLastError();
+}
+
 }  // namespace lbm
