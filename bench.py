@@ -400,6 +400,8 @@ def serving_measurement(capacity_mlups, n_requests, stream="scaled"):
     free, _ = torch.cuda.mem_get_info()
     srv = serving.run_stream([dict(s) for s in specs], budget_bytes=int(0.5 * free), max_slots=32, steps_per_tick=32)
     b2b = serving.run_back_to_back([dict(s) for s in specs], "fp32")
+    # the same arm with each request in its own storage precision (FP32 or FP16S, as served)
+    b2b_own = serving.run_back_to_back([dict(s) for s in specs], None)
     # the same stream at 0.5x the capacity: latency when the server is not saturated
     low = I.serving_requests(n=n_requests, seed=2204, rate=rate * 0.5 / 1.2, d_range=d_range,
                              steps_range=steps_range)
@@ -417,7 +419,10 @@ def serving_measurement(capacity_mlups, n_requests, stream="scaled"):
         "p50_s": srv["latency_p50_s"], "p99_s": srv["latency_p99_s"],
         "aggregate_mlups": srv["mlups"], "makespan_s": srv["makespan_s"],
         "back_to_back_fp32_mlups": b2b["mlups"], "back_to_back_s": b2b["seconds"],
+        "back_to_back_setup_s": b2b["setup_seconds"],
         "speedup_vs_back_to_back": srv["mlups"] / b2b["mlups"],
+        "back_to_back_own_precision_mlups": b2b_own["mlups"],
+        "speedup_vs_back_to_back_own_precision": srv["mlups"] / b2b_own["mlups"],
         "steps_per_tick": 32, "graph_captures": srv["info"]["graph_captures"],
         "graph_launches": srv["info"]["graph_launches"],
     }

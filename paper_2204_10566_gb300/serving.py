@@ -83,19 +83,25 @@ def run_stream(specs, budget_bytes, max_slots=32, steps_per_tick=32, precision=N
 
 def run_back_to_back(specs, precision="fp32"):
     """The same requests one after another as plain single-lattice runs
-    (geometry set-up, steps, readback of rho and u), in arrival order."""
+    (geometry set-up, steps, readback of rho and u), in arrival order.
+    precision None runs each request in its own storage precision.  Also
+    returns the seconds spent outside the steps and readback (index build,
+    allocation, initialisation, release)."""
     import torch
 
     t0 = time.perf_counter()
     updates = 0.0
+    run_s = 0.0
     for s in sorted(specs, key=lambda s: s["arrival"]):
         flags = request_geometry(s)
-        with lbm.Lattice(flags, precision) as G:
+        with lbm.Lattice(flags, precision or s["precision"]) as G:
             G.set_params(**request_params(s))
-            G.init_equilibrium(1.0, (0.0, 0.0, 0.0))
+            G.init_equilibrium(1.0, (0.0, 0.0, 0.0)).sync()
+            t1 = time.perf_counter()
             G.step(s["steps"])
             G.moments()
+            run_s += time.perf_counter() - t1
             updates += G.n_active * s["steps"]
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return dict(cell_updates=updates, seconds=dt, mlups=updates / dt / 1e6)
+    return dict(cell_updates=updates, seconds=dt, mlups=updates / dt / 1e6, setup_seconds=dt - run_s)
